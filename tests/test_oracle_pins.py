@@ -1,0 +1,374 @@
+"""Pins for the FP64 oracle: each test checks the oracle against something other
+than itself -- what the convolution's definition (paper Sec. 1 / Sec. 5.A:
+six nested loops; Sec. 5.B: forward and backward passes) and plain mathematics
+fix -- so that a dropped term, a wrong sign or index, or a transposed operand
+fails at least one of them.
+
+* 1x1 identity filters reproduce the input exactly;
+* delta filters shift the input exactly (pins stride, padding, dilation);
+* linearity in x and in w;
+* integer-valued inputs give exact sums, equal to the rounded FFT result;
+* brute-force FFT cross-correlation agrees to 1e-12 on tiny inputs;
+* torch.nn.functional.conv2d in float64 (a library special case, test only);
+* adjoint identities <conv(x,w), g> = <x, dgrad(g,w)> = <w, wgrad(x,g)>;
+* central finite differences of L = sum g*y give dx, dw, db;
+* the quantisers against their format definitions and torch's converters.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import Conv
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _to_layout(a_nchw, layout):
+    return a_nchw if layout == "NCHW" else np.ascontiguousarray(a_nchw.transpose(0, 2, 3, 1))
+
+
+def _from_layout(a, layout):
+    return a if layout == "NCHW" else np.ascontiguousarray(a.transpose(0, 3, 1, 2))
+
+
+def _fft_conv(x, w, b, stride, pad, dil):
+    """Cross-correlation via numpy FFT on NCHW / KCRS float64 arrays.
+
+    Correlation with w equals convolution with w flipped in both spatial axes.
+    The dilated filter has d-1 zeros between taps. The stride subsamples the
+    stride-1 result."""
+    N, C, H, W = x.shape
+    K, _, R, S = w.shape
+    (u, v), (ph, pw), (dh, dw) = stride, pad, dil
+    xp = np.zeros((N, C, H + 2 * ph, W + 2 * pw))
+    xp[:, :, ph:ph + H, pw:pw + W] = x
+    Rd, Sd = dh * (R - 1) + 1, dw * (S - 1) + 1
+    wd = np.zeros((K, C, Rd, Sd))
+    wd[:, :, ::dh, ::dw] = w
+    Hp, Wp = xp.shape[2:]
+    fh, fw = Hp + Rd - 1, Wp + Sd - 1
+    X = np.fft.rfft2(xp, s=(fh, fw))                      # N C fh fw'
+    Wf = np.fft.rfft2(wd[:, :, ::-1, ::-1], s=(fh, fw))   # K C fh fw'
+    Y = np.einsum("ncij,kcij->nkij", X, Wf)
+    full = np.fft.irfft2(Y, s=(fh, fw))
+    valid = full[:, :, Rd - 1:Hp, Sd - 1:Wp]              # stride-1 correlation
+    P = (H + 2 * ph - Rd) // u + 1
+    Q = (W + 2 * pw - Sd) // v + 1
+    y = valid[:, :, ::u, ::v][:, :, :P, :Q]
+    if b is not None:
+        y = y + b[None, :, None, None]
+    return y
+
+
+CASES = [
+    # N, C, H, W, K, R, S, stride, pad, dil
+    (1, 1, 5, 5, 1, 3, 3, (1, 1), (1, 1), (1, 1)),
+    (2, 3, 7, 6, 4, 3, 3, (1, 1), (1, 1), (1, 1)),
+    (2, 3, 9, 9, 2, 3, 3, (2, 2), (1, 1), (1, 1)),
+    (1, 4, 9, 8, 3, 3, 2, (1, 2), (0, 1), (2, 1)),
+    (2, 2, 8, 9, 3, 1, 1, (2, 1), (0, 0), (1, 1)),
+    (1, 3, 9, 9, 2, 5, 5, (1, 1), (2, 2), (1, 1)),
+    (1, 2, 9, 9, 2, 3, 3, (2, 2), (2, 2), (2, 2)),
+    (2, 4, 6, 6, 4, 2, 2, (1, 1), (0, 1), (1, 1)),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("layout", ["NCHW", "NHWC"])
+def test_fft_bruteforce(case, layout):
+    N, C, H, W, K, R, S, st, pd, dl = case
+    p = Conv(N, C, H, W, K, R, S, st, pd, dl, layout)
+    r = _rng(hash(case) % 2**32)
+    x = r.uniform(-1, 1, (N, C, H, W))
+    w = r.uniform(-1, 1, (K, C, R, S))
+    b = r.uniform(-0.1, 0.1, K)
+    ref = _fft_conv(x, w, b, st, pd, dl)
+    y = oracle.conv2d_fwd(p, _to_layout(x, layout), _to_layout(w, layout), b)
+    y = _from_layout(y, layout)
+    assert y.shape == ref.shape
+    assert np.max(np.abs(y - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_torch_fp64_special_case(case):
+    N, C, H, W, K, R, S, st, pd, dl = case
+    p = Conv(N, C, H, W, K, R, S, st, pd, dl, "NCHW")
+    r = _rng(7)
+    x = r.normal(size=(N, C, H, W))
+    w = r.normal(size=(K, C, R, S))
+    b = r.normal(size=K)
+    ref = torch.nn.functional.conv2d(torch.from_numpy(x), torch.from_numpy(w),
+                                     torch.from_numpy(b), stride=st, padding=pd,
+                                     dilation=dl).numpy()
+    y = oracle.conv2d_fwd(p, x, w, b)
+    assert np.max(np.abs(y - ref)) < 1e-11
+
+
+@pytest.mark.parametrize("layout", ["NCHW", "NHWC"])
+def test_identity_1x1(layout):
+    N, C, H, W = 2, 5, 7, 6
+    p = Conv(N, C, H, W, C, 1, 1, 1, 0, 1, layout)
+    x = _rng(1).normal(size=(N, C, H, W))
+    w = np.eye(C).reshape(C, C, 1, 1)
+    y = oracle.conv2d_fwd(p, _to_layout(x, layout), _to_layout(w, layout))
+    assert np.array_equal(_from_layout(y, layout), x)
+
+
+@pytest.mark.parametrize("layout", ["NCHW", "NHWC"])
+@pytest.mark.parametrize("st,pd,dl,R,S", [
+    ((1, 1), (1, 1), (1, 1), 3, 3),
+    ((2, 2), (1, 1), (1, 1), 3, 3),
+    ((1, 2), (2, 1), (2, 1), 3, 3),
+    ((2, 1), (0, 3), (1, 3), 2, 3),
+    ((1, 1), (3, 3), (1, 1), 7, 7),
+])
+def test_delta_filter_shift(layout, st, pd, dl, R, S):
+    N, C, H, W = 2, 3, 9, 10
+    r = _rng(2)
+    x = r.normal(size=(N, C, H, W))
+    for r0, s0 in itertools.product(range(R), range(S)):
+        p = Conv(N, C, H, W, C, R, S, st, pd, dl, layout)
+        w = np.zeros((C, C, R, S))
+        for c in range(C):
+            w[c, c, r0, s0] = 1.0
+        y = _from_layout(oracle.conv2d_fwd(p, _to_layout(x, layout), _to_layout(w, layout)),
+                         layout)
+        # y[n,c,p,q] = x[n,c, p*u + r0*dh - ph, q*v + s0*dw - pw] (zero outside)
+        exp = np.zeros((N, C, p.P, p.Q))
+        for pp in range(p.P):
+            for qq in range(p.Q):
+                h = pp * st[0] + r0 * dl[0] - pd[0]
+                ww = qq * st[1] + s0 * dl[1] - pd[1]
+                if 0 <= h < H and 0 <= ww < W:
+                    exp[:, :, pp, qq] = x[:, :, h, ww]
+        assert np.array_equal(y, exp), (r0, s0)
+
+
+def test_linearity():
+    p = Conv(2, 3, 8, 8, 4, 3, 3, 1, 1, 1, "NHWC")
+    r = _rng(3)
+    x1, x2 = r.normal(size=p.x_shape), r.normal(size=p.x_shape)
+    w1, w2 = r.normal(size=p.w_shape), r.normal(size=p.w_shape)
+    a, b = 0.75, -2.5
+    lhs = oracle.conv2d_fwd(p, a * x1 + b * x2, w1)
+    rhs = a * oracle.conv2d_fwd(p, x1, w1) + b * oracle.conv2d_fwd(p, x2, w1)
+    scale = np.max(np.abs(rhs))
+    assert np.max(np.abs(lhs - rhs)) < 1e-13 * scale
+    lhs = oracle.conv2d_fwd(p, x1, a * w1 + b * w2)
+    rhs = a * oracle.conv2d_fwd(p, x1, w1) + b * oracle.conv2d_fwd(p, x1, w2)
+    assert np.max(np.abs(lhs - rhs)) < 1e-13 * scale
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_integer_exact(case):
+    """Integer inputs: every product and partial sum is an integer well below
+    2^53, so the oracle's sum is exact and must equal the FFT result rounded
+    to the nearest integer (FFT error << 0.5)."""
+    N, C, H, W, K, R, S, st, pd, dl = case
+    p = Conv(N, C, H, W, K, R, S, st, pd, dl, "NCHW")
+    r = _rng(4)
+    x = r.integers(-4, 5, (N, C, H, W)).astype(np.float64)
+    w = r.integers(-4, 5, (K, C, R, S)).astype(np.float64)
+    b = r.integers(-8, 9, K).astype(np.float64)
+    y = oracle.conv2d_fwd(p, x, w, b)
+    ref = np.rint(_fft_conv(x, w, b, st, pd, dl))
+    assert np.array_equal(y, ref)
+    assert np.array_equal(y, np.rint(y))
+
+
+def test_relu_and_bound():
+    p = Conv(2, 3, 7, 7, 4, 3, 3, 1, 1, 1, "NHWC")
+    r = _rng(5)
+    x, w, b = r.normal(size=p.x_shape), r.normal(size=p.w_shape), r.normal(size=4)
+    y, bound = oracle.conv2d_fwd(p, x, w, b, with_bound=True)
+    yr = oracle.conv2d_fwd(p, x, w, b, relu=True)
+    assert np.array_equal(yr, np.maximum(y, 0.0))
+    assert np.all(np.abs(y) <= bound * (1 + 1e-15))
+    # with non-negative x, w, b the bound is the sum itself
+    y2, bound2 = oracle.conv2d_fwd(p, np.abs(x), np.abs(w), np.abs(b), with_bound=True)
+    assert np.max(np.abs(y2 - bound2)) <= 1e-13 * np.max(bound2)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_adjoint_identities(case):
+    N, C, H, W, K, R, S, st, pd, dl = case
+    for layout in ("NCHW", "NHWC"):
+        p = Conv(N, C, H, W, K, R, S, st, pd, dl, layout)
+        r = _rng(6)
+        x, w, g = r.normal(size=p.x_shape), r.normal(size=p.w_shape), r.normal(size=p.y_shape)
+        y = oracle.conv2d_fwd(p, x, w)
+        lhs = np.sum(y * g)
+        dx = oracle.conv2d_dgrad(p, g, w)
+        dw = oracle.conv2d_wgrad(p, x, g)
+        scale = np.sum(np.abs(y * g)) + 1.0
+        assert abs(lhs - np.sum(x * dx)) < 1e-12 * scale
+        assert abs(lhs - np.sum(w * dw)) < 1e-12 * scale
+        db = oracle.conv2d_bgrad(p, g)
+        kax = 1 if layout == "NCHW" else 3
+        axes = tuple(a for a in range(4) if a != kax)
+        assert np.max(np.abs(db - g.sum(axis=axes))) < 1e-12 * (np.abs(g).sum() + 1)
+
+
+@pytest.mark.parametrize("layout", ["NCHW", "NHWC"])
+@pytest.mark.parametrize("st,pd,dl", [((1, 1), (1, 1), (1, 1)), ((2, 2), (1, 1), (1, 1)),
+                                      ((1, 2), (2, 0), (2, 1))])
+def test_central_finite_differences(layout, st, pd, dl):
+    """L = sum g*y is linear in each of x, w, b separately, so a central
+    difference with a power-of-two step is exact up to roundoff. Size: N=1,
+    C=K=4, H=W=6, 3x3 (the backward workload's tiny check)."""
+    p = Conv(1, 4, 6, 6, 4, 3, 3, st, pd, dl, layout)
+    r = _rng(8)
+    x, w, b = r.normal(size=p.x_shape), r.normal(size=p.w_shape), r.normal(size=4)
+    g = r.normal(size=p.y_shape)
+    h = 2.0 ** -10
+
+    def L(xx, ww, bb):
+        return float(np.sum(oracle.conv2d_fwd(p, xx, ww, bb, nthreads=1) * g))
+
+    def fd(arr, which):
+        out = np.empty(arr.size)
+        flat = arr.reshape(-1)
+        for i in range(arr.size):
+            keep = flat[i]
+            flat[i] = keep + h
+            lp = L(x, w, b)
+            flat[i] = keep - h
+            lm = L(x, w, b)
+            flat[i] = keep
+            out[i] = (lp - lm) / (2 * h)
+        return out.reshape(arr.shape)
+
+    dx_fd, dw_fd, db_fd = fd(x, "x"), fd(w, "w"), fd(b, "b")
+    dx = oracle.conv2d_dgrad(p, g, w)
+    dw = oracle.conv2d_wgrad(p, x, g)
+    db = oracle.conv2d_bgrad(p, g)
+    scale = np.sum(np.abs(g)) * max(np.max(np.abs(x)), np.max(np.abs(w)), 1.0)
+    assert np.max(np.abs(dx - dx_fd)) < 1e-9 * scale
+    assert np.max(np.abs(dw - dw_fd)) < 1e-9 * scale
+    assert np.max(np.abs(db - db_fd)) < 1e-9 * scale
+
+
+@pytest.mark.parametrize("layout", ["NCHW", "NHWC"])
+def test_points_equal_full(layout):
+    p = Conv(2, 5, 9, 7, 6, 3, 3, (2, 1), (1, 1), (1, 2), layout)
+    r = _rng(9)
+    x, w, b = r.normal(size=p.x_shape), r.normal(size=p.w_shape), r.normal(size=6)
+    g = r.normal(size=p.y_shape)
+    y, yb = oracle.conv2d_fwd(p, x, w, b, relu=True, with_bound=True)
+    idx = r.choice(y.size, 50, replace=False)
+    yp, ypb = oracle.conv2d_fwd(p, x, w, b, relu=True, idx=idx, with_bound=True)
+    assert np.array_equal(yp, y.reshape(-1)[idx]) and np.array_equal(ypb, yb.reshape(-1)[idx])
+    dx = oracle.conv2d_dgrad(p, g, w)
+    idx = r.choice(dx.size, 50, replace=False)
+    assert np.array_equal(oracle.conv2d_dgrad(p, g, w, idx=idx), dx.reshape(-1)[idx])
+    dw = oracle.conv2d_wgrad(p, x, g)
+    idx = r.choice(dw.size, 50, replace=False)
+    assert np.array_equal(oracle.conv2d_wgrad(p, x, g, idx=idx), dw.reshape(-1)[idx])
+
+
+def test_layouts_agree():
+    p0 = Conv(2, 3, 8, 7, 5, 3, 2, (1, 2), (1, 0), (2, 1), "NCHW")
+    p1 = Conv(2, 3, 8, 7, 5, 3, 2, (1, 2), (1, 0), (2, 1), "NHWC")
+    r = _rng(10)
+    x, w, b = r.normal(size=p0.x_shape), r.normal(size=p0.w_shape), r.normal(size=5)
+    y0 = oracle.conv2d_fwd(p0, x, w, b)
+    y1 = oracle.conv2d_fwd(p1, _to_layout(x, "NHWC"), _to_layout(w, "NHWC"), b)
+    assert np.array_equal(y0, _from_layout(y1, "NHWC"))
+
+
+def test_output_dims():
+    for (H, R, pad, dil, st) in [(56, 3, 1, 1, 2), (56, 1, 0, 1, 1), (7, 7, 3, 1, 2),
+                                 (112, 5, 2, 1, 2), (32, 3, 1, 1, 1), (6, 3, 0, 2, 1)]:
+        p = Conv(1, 1, H, H, 1, R, R, st, pad, dil)
+        ref = torch.nn.functional.conv2d(torch.zeros(1, 1, H, H), torch.zeros(1, 1, R, R),
+                                         stride=st, padding=pad, dilation=dil).shape[2]
+        assert p.P == ref and p.Q == ref
+    with pytest.raises(ValueError):
+        Conv(1, 1, 2, 2, 1, 5, 5, 1, 0, 1)
+
+
+# ---- quantisers ----
+
+def test_bf16_rounding_matches_definition_and_torch():
+    r = _rng(11)
+    vals = np.concatenate([
+        r.normal(size=20000).astype(np.float32),
+        (r.normal(size=2000) * 1e-39).astype(np.float32),          # subnormals
+        np.array([0.0, -0.0, 1.0, -1.0, 3.4e38, -3.4e38, np.inf, -np.inf], np.float32),
+    ])
+    # exact ties: values halfway between two bf16 neighbours
+    base = r.integers(0, 0x7F80, 1000).astype(np.uint32) << 16    # finite patterns
+    ties = (base | 0x8000).view(np.float32)
+    vals = np.concatenate([vals, ties])
+    got = oracle.round_bf16_bits(vals)
+    ref = torch.from_numpy(vals).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(got, ref)
+    # ties go to the even neighbour
+    tb = oracle.round_bf16_bits(ties)
+    assert np.all((tb & 1) == 0)
+    # nan stays nan
+    assert np.isnan(oracle.round_bf16(np.array([np.nan], np.float32)))[0]
+
+
+def test_e4m3_codes_roundtrip():
+    codes = np.arange(256, dtype=np.uint8)
+    vals = oracle.e4m3_to_f64(codes)
+    nan = (codes & 0x7F) == 0x7F
+    assert np.all(np.isnan(vals[nan])) and not np.any(np.isnan(vals[~nan]))
+    assert np.max(vals[~nan]) == 448.0 and np.min(vals[~nan]) == -448.0
+    assert vals[1] == 2.0 ** -9                      # smallest subnormal
+    assert vals[0x08] == 2.0 ** -6                   # smallest normal
+    back = oracle.quant_e4m3(vals[~nan].astype(np.float32))
+    assert np.array_equal(back, codes[~nan])
+    # decoding agrees with torch's float8_e4m3fn interpretation of the same bits
+    tv = torch.from_numpy(codes[~nan].copy()).view(torch.float8_e4m3fn).to(torch.float64)
+    assert np.array_equal(tv.numpy(), vals[~nan])
+
+
+def test_e4m3_rounding_ties_and_saturation():
+    codes = np.arange(0, 0x7E, dtype=np.uint8)      # positive finite codes, ascending
+    v = oracle.e4m3_to_f64(np.arange(0, 0x7F, dtype=np.uint8))
+    mids = ((v[:-1] + v[1:]) / 2).astype(np.float32)
+    assert np.array_equal(mids.astype(np.float64), (v[:-1] + v[1:]) / 2)  # exact in fp32
+    got = oracle.quant_e4m3(mids)
+    lo, hi = codes, codes + 1
+    want = np.where(lo % 2 == 0, lo, hi).astype(np.uint8)
+    assert np.array_equal(got, want)
+    big = np.array([448.0, 449.0, 463.9, 464.0, 1e6, np.float32(3e38)], np.float32)
+    assert np.all(oracle.quant_e4m3(big) == 0x7E)
+    assert np.all(oracle.quant_e4m3(-big) == 0xFE)
+
+
+def test_e4m3_matches_torch_within_range():
+    r = _rng(12)
+    vals = np.concatenate([r.normal(size=50000) * 60, r.normal(size=5000) * 1e-2,
+                           r.normal(size=5000) * 1e-3]).astype(np.float32)
+    vals = np.clip(vals, -448, 448)
+    got = oracle.e4m3_to_f64(oracle.quant_e4m3(vals))
+    ref = torch.from_numpy(vals).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    assert np.array_equal(got, ref)
+
+
+def test_scale_quant_definition():
+    r = _rng(13)
+    a = (r.normal(size=(6, 300)) * r.uniform(0.01, 10, (6, 1))).astype(np.float32)
+    a[2] = 0.0
+    codes, scales = oracle.scale_quant_e4m3(a, 6)
+    amax = np.max(np.abs(a), axis=1)
+    want = np.maximum((amax / np.float32(448.0)).astype(np.float32), np.float32(1e-12))
+    assert np.array_equal(scales, want)
+    vals = oracle.e4m3_to_f64(codes)
+    # the largest-magnitude element of each row lands on +-448 (or near it)
+    for i in range(6):
+        if amax[i] > 0:
+            assert np.max(np.abs(vals[i])) >= 416.0
+    assert np.all(vals[2] == 0)
+    # dequantised values are close to the input (3 mantissa bits: rel err <= 2^-4)
+    deq = vals * scales[:, None]
+    big = np.abs(a) > scales[:, None] * 2.0 ** -6 * 4
+    assert np.all(np.abs(deq - a)[big] <= np.abs(a)[big] * 2.0 ** -4 * (1 + 1e-6))
