@@ -1,0 +1,598 @@
+"""Throughput of the GB300 convolution library on the ResNet-50 bottleneck layer
+set (BF16 NHWC, batch 32, bias + ReLU), plus the plain FP32 kernel on the same
+layers, the FP8 workload, the grouped 64-problem launch and the backward pass.
+
+One JSON line on rank 0. A "step" is one forward pass over the four layers
+(1x1 256->64, 3x3 64->64, 1x1 64->256 at 56x56, 3x3 stride-2 128->128
+56->28), each on its own synthetic batch. The timed region replays a CUDA
+graph holding K steps; inputs rotate over four buffer sets (~750 MB in all,
+well over the 129 MB L2), so every step reads its inputs from HBM.
+
+--impl reference times the FP64 CPU oracle (the "reference arm" of this
+comparison) on a bounded sample of the same workload on the host's cores.
+Under torchrun every rank runs the same per-rank workload (weak scaling; the
+layers shard over the batch with no exchange); rank 0 reports the total.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return dict(PEAKS_FALLBACK), "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampling (nvidia-smi) during the measured region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0, t1):
+        rows = [p for (t, p) in self.rows if t0 <= t <= t1] or [p for (_, p) in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+
+        sm = sorted(v for v in (num(r[1]) for r in rows) if v is not None)
+        smax = max((v for v in (num(r[2]) for r in rows) if v is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        pw = [v for v in (num(r[3]) for r in rows) if v is not None]
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def layer_bytes(sh, eb_in, eb_out):
+    x = sh.N * sh.H * sh.W * sh.C * eb_in
+    w = sh.K * sh.R * sh.S * sh.C * eb_in
+    y = sh.N * sh.P * sh.Q * sh.K * eb_out
+    return x + w + sh.K * 4 + y
+
+
+class Layer:
+    """One convolution with its buffer sets, launched through the C ABI."""
+
+    def __init__(self, sh, dtype, sets, seed, dev, relu=True):
+        import torch
+        from paper_2207_00257_gb300 import binding as B
+        from paper_2207_00257_gb300.synth import make_inputs
+        self.sh = sh
+        self.dtype = dtype
+        self.xs, self.ys = [], []
+        x, w, b, _ = make_inputs(sh, seed)
+        self.x_master = x
+        self.w = w.to(dtype).to(dev)
+        self.b = b.to(dev)
+        self.w_master = w
+        self.b_master = b
+        for i in range(sets):
+            xi = x if i == 0 else make_inputs(sh, seed + 7919 * i, bias=False)[0]
+            self.xs.append(xi.to(dtype).to(dev))
+            self.ys.append(torch.empty(sh.y_shape(), dtype=dtype, device=dev))
+        ind = {torch.bfloat16: B.GBCONV_BF16, torch.float32: B.GBCONV_F32}[dtype]
+        self.prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                              ind, ind, B.GBCONV_NHWC,
+                              B.GBCONV_FLAG_BIAS | (B.GBCONV_FLAG_RELU if relu else 0))
+        self.B = B
+
+    def launch(self, i, stream):
+        s = self.B.conv2d_fwd(self.prob, self.xs[i].data_ptr(), self.w.data_ptr(),
+                              self.b.data_ptr(), 0, 0, self.ys[i].data_ptr(), 0, 0, stream)
+        self.B.check(s, "conv2d_fwd")
+
+
+def capture_steps(launch_fns, steps, nsets, torch, timed_events=True):
+    """Captures `steps` steps into one CUDA graph. launch_fns: list of
+    callables f(set_index, stream). Returns (graph, events[steps][len][2])."""
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in launch_fns] for _ in range(steps)] if timed_events else None
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            for st in range(steps):
+                for j, f in enumerate(launch_fns):
+                    if timed_events:
+                        evs[st][j][0].record(stream)
+                    f(st % nsets, stream.cuda_stream)
+                    if timed_events:
+                        evs[st][j][1].record(stream)
+    return g, evs
+
+
+def replay_timed(g, torch, dist_on):
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    start.record()
+    g.replay()
+    end.record()
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    return start.elapsed_time(end), t0, t1
+
+
+def max_over_ranks(v, torch, dist_on):
+    if not dist_on:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def bench_layers(layers, steps, warmup, nsets, torch, dist_on, sampler=None):
+    """Times `steps` graph-replayed steps over `layers`. Returns dict with
+    ms_per_step and per-layer average launch durations (us)."""
+    fns = [lay.launch for lay in layers]
+    # warm-up: eager steps (sets attributes, tensor maps), then graph warm-up replays
+    for st in range(max(warmup, 1)):
+        for f in fns:
+            f(st % nsets, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    gw, _ = capture_steps(fns, nsets, nsets, torch, timed_events=False)
+    for _ in range(max(warmup, 1)):
+        gw.replay()
+    torch.cuda.synchronize()
+    g, evs = capture_steps(fns, steps, nsets, torch)
+    g.replay()  # one untimed replay of the timed graph itself
+    torch.cuda.synchronize()
+    ms, t0, t1 = replay_timed(g, torch, dist_on)
+    ms = max_over_ranks(ms, torch, dist_on)
+    per = [sum(evs[s][j][0].elapsed_time(evs[s][j][1]) for s in range(steps)) / steps * 1e3
+           for j in range(len(fns))]
+    return {"ms_total": ms, "ms_per_step": ms / steps, "launch_us": per, "t0": t0, "t1": t1}
+
+
+def resnet_report(layers, res, pk, eb):
+    out = []
+    for lay, us in zip(layers, res["launch_us"]):
+        sh = lay.sh
+        by = layer_bytes(sh, eb, eb)
+        tf = sh.flops / (us * 1e-6) / 1e12
+        gbs = by / (us * 1e-6) / 1e9
+        ai = sh.flops / by
+        attain = min(pk["bf16_tflops"], ai * pk["hbm_gbs"] / 1e3)
+        out.append({"layer": sh.tag, "us": round(us, 2), "tflops": round(tf, 1),
+                    "gbs": round(gbs, 1), "ai_flop_per_byte": round(ai, 1),
+                    "frac_of_bf16_peak": round(tf / pk["bf16_tflops"], 4),
+                    "frac_of_hbm": round(gbs / pk["hbm_gbs"], 4),
+                    "frac_of_attainable": round(tf / attain, 4),
+                    "bound": "hbm" if ai * pk["hbm_gbs"] / 1e3 < pk["bf16_tflops"] else "tensor"})
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline BF16 layer set (skip FP32/FP8/grouped/backward)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2207_00257_gb300.synth import resnet_layers
+    dev = torch.device("cuda", local)
+    pk, pk_kind = peaks()
+    nsets = 4
+    layers = [Layer(sh, torch.bfloat16, nsets, 100 + i + 1000 * rank, dev)
+              for i, sh in enumerate(resnet_layers(32))]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    res = bench_layers(layers, args.steps, args.warmup, nsets, torch, dist_on)
+    flops_step = sum(l.sh.flops for l in layers)
+    value = flops_step * args.steps * world / (res["ms_total"] * 1e-3) / 1e12
+    per_layer = resnet_report(layers, res, pk, 2)
+    # dominant kernel: the launch with the largest time share
+    j = max(range(len(layers)), key=lambda i: res["launch_us"][i])
+    dom = per_layer[j]
+    sh = layers[j].sh
+    if dom["bound"] == "tensor":
+        roof = {"bound": "tensor", "achieved": dom["tflops"], "peak": pk["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": round(dom["tflops"] / pk["bf16_tflops"], 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": dom["gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(dom["gbs"] / pk["hbm_gbs"], 4)}
+    roof.update({"kernel": f"tc_fwd_kernel ({sh.tag})", "traffic": None,
+                 "algorithmic_bytes_per_launch": layer_bytes(sh, 2, 2),
+                 "flops_per_launch": sh.flops, "peak_source": pk_kind + " (burst)"})
+    clocks_window = (res["t0"], res["t1"])
+    out = {
+        "metric": "conv2d TFLOP/s & % of tensor peak, BF16/FP8 vs FP32 at stated rel err",
+        "value": round(value, 2), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(res["ms_per_step"], 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded N(0,1) activations, He-normal weights, U[-0.1,0.1] bias)",
+        "config": {"workload": "resnet50_bottleneck_layers_bf16_nhwc_batch32",
+                   "layers": [l.sh.tag for l in layers], "global_batch": 32 * world,
+                   "per_gpu_batch": 32, "epilogue": "bias+relu", "accumulate": "fp32",
+                   "l2": f"inputs/outputs rotated over {nsets} buffer sets "
+                         f"({nsets * sum(layer_bytes(l.sh, 2, 2) for l in layers) / 1e6:.0f} MB > 129 MB L2)",
+                   "timing": "CUDA graph of K steps, CUDA events on the launch stream",
+                   "parallelism": f"dp{world} (batch shards, no exchange)"},
+        "frac_of_bf16_peak": round(value / world / pk["bf16_tflops"], 4),
+        "layers": per_layer,
+        "roofline": roof,
+        "gpu_launches": len(layers) * args.steps,
+    }
+    # ---- e2e through the public API with host buffers ----
+    out["e2e"] = e2e_resnet(layers, torch, dist_on, world, max(3, min(args.steps, 20)))
+    # ---- extras: FP32 kernel, FP8, grouped, backward ----
+    if not args.no_extras:
+        out["fp32"] = bench_fp32(torch, dev, args, dist_on, pk)
+        out["fp8"] = bench_fp8(torch, dev, args, dist_on, pk)
+        out["grouped"] = bench_grouped(torch, dev, args, dist_on, pk)
+        out["backward"] = bench_backward(torch, dev, args, dist_on, pk)
+    sampler.stop()
+    out["clocks"] = sampler.summary(*clocks_window)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(layers, torch)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist_on:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e_resnet(layers, torch, dist_on, world, steps):
+    """Same metric through the user call: per step, pinned host -> device copy
+    of each layer's input, conv2d_fwd, device -> pinned host copy of y."""
+    from paper_2207_00257_gb300 import functional as F
+    hx = [l.xs[0].cpu().pin_memory() for l in layers]
+    hy = [torch.empty(l.ys[0].shape, dtype=l.ys[0].dtype).pin_memory() for l in layers]
+    dx = [torch.empty_like(l.xs[0]) for l in layers]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for l, h, d, o in zip(layers, hx, dx, hy):
+            d.copy_(h, non_blocking=True)
+            y = F.conv2d(d, l.w, l.b, l.sh.stride, l.sh.pad, l.sh.dil, True, "NHWC", out=l.ys[0])
+            o.copy_(y, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), torch, dist_on)
+    flops = sum(l.sh.flops for l in layers) * steps * world
+    h2d = sum(t.numel() * t.element_size() for t in hx)
+    d2h = sum(t.numel() * t.element_size() for t in hy)
+    return {"value": round(flops / (ms * 1e-3) / 1e12, 2), "unit": "TFLOP/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "ms_per_step": round(ms / steps, 4)}
+
+
+def bench_fp32(torch, dev, args, dist_on, pk):
+    from paper_2207_00257_gb300.synth import resnet_layers
+    layers = [Layer(sh, torch.float32, 2, 100 + i, dev) for i, sh in enumerate(resnet_layers(32))]
+    steps = max(3, min(args.steps, 20))
+    res = bench_layers(layers, steps, 3, 2, torch, dist_on)
+    flops = sum(l.sh.flops for l in layers)
+    prop = torch.cuda.get_device_properties(dev)
+    # FP32 CUDA-core peak: 128 FFMA lanes per SM x 2 flops x SMs x max SM clock
+    fp32_peak = 2 * 128 * prop.multi_processor_count * 2.070e9 / 1e12
+    v = flops / (res["ms_per_step"] * 1e-3) / 1e12
+    rows = []
+    for lay, us in zip(layers, res["launch_us"]):
+        rows.append({"layer": lay.sh.tag, "us": round(us, 1),
+                     "tflops": round(lay.sh.flops / (us * 1e-6) / 1e12, 2)})
+    del layers
+    torch.cuda.empty_cache()
+    return {"tflops": round(v, 2), "ms_per_step": round(res["ms_per_step"], 4),
+            "fp32_peak_tflops": round(fp32_peak, 1),
+            "fp32_peak_note": "2 x 128 FFMA lanes x SMs x 2070 MHz (max clock)",
+            "frac_of_fp32_peak": round(v / fp32_peak, 4), "layers": rows,
+            "kernel": "simt_igemm (FP32 FFMA, no tensor cores)"}
+
+
+def bench_fp8(torch, dev, args, dist_on, pk):
+    from paper_2207_00257_gb300 import binding as B
+    from paper_2207_00257_gb300.synth import config_fp8, make_inputs
+    sh = config_fp8()
+    x, w, b, _ = make_inputs(sh, 3, "relu_normal", "he")
+    nsets = 2
+    xs = [x.to(dev)] + [make_inputs(sh, 3 + 11 * i, "relu_normal", "he", bias=False)[0].to(dev)
+                        for i in range(1, nsets)]
+    xq = [torch.empty(sh.x_shape(), dtype=torch.uint8, device=dev) for _ in range(nsets)]
+    xsc = [torch.empty(1, dtype=torch.float32, device=dev) for _ in range(nsets)]
+    wq = torch.empty(sh.w_shape(), dtype=torch.uint8, device=dev)
+    wsc = torch.empty(sh.K, dtype=torch.float32, device=dev)
+    wd = w.to(dev)
+    st = torch.cuda.current_stream().cuda_stream
+    B.check(B.gbconv_quantize_e4m3(wd.data_ptr(), B.GBCONV_F32, sh.K, wd.numel() // sh.K,
+                                   wq.data_ptr(), wsc.data_ptr(), st), "quant w")
+    bd = b.to(dev)
+    ys = [torch.empty(sh.y_shape(), dtype=torch.bfloat16, device=dev) for _ in range(nsets)]
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                     B.GBCONV_E4M3, B.GBCONV_BF16, B.GBCONV_NHWC, B.GBCONV_FLAG_BIAS)
+
+    def quant(i, stream):
+        B.check(B.gbconv_quantize_e4m3(xs[i].data_ptr(), B.GBCONV_F32, 1, xs[i].numel(),
+                                       xq[i].data_ptr(), xsc[i].data_ptr(), stream), "quant x")
+
+    def conv(i, stream):
+        B.check(B.conv2d_fwd(prob, xq[i].data_ptr(), wq.data_ptr(), bd.data_ptr(),
+                             xsc[i].data_ptr(), wsc.data_ptr(), ys[i].data_ptr(), 0, 0, stream),
+                "fp8 conv")
+
+    class L:
+        def __init__(s, f):
+            s.launch = f
+
+    steps = max(3, min(args.steps, 50))
+    res = bench_layers([L(quant), L(conv)], steps, 3, nsets, torch, dist_on)
+    conv_us = res["launch_us"][1]
+    tf_conv = sh.flops / (conv_us * 1e-6) / 1e12
+    tf_step = sh.flops / (res["ms_per_step"] * 1e-3) / 1e12
+    fp8_peak = 2 * pk["bf16_tflops"]
+    return {"workload": sh.tag, "tflops_conv_kernel": round(tf_conv, 1),
+            "tflops_with_activation_quantisation": round(tf_step, 1),
+            "conv_us": round(conv_us, 2), "quant_us": round(res["launch_us"][0], 2),
+            "fp8_peak_tflops": round(fp8_peak, 1),
+            "fp8_peak_note": "2 x measured BF16 burst (the dense FP8:BF16 tensor-rate ratio)",
+            "frac_of_fp8_peak": round(tf_conv / fp8_peak, 4)}
+
+
+def bench_grouped(torch, dev, args, dist_on, pk):
+    from paper_2207_00257_gb300 import binding as B
+    from paper_2207_00257_gb300.synth import grouped_problems, make_inputs
+    shapes = grouped_problems()
+    xs, ws, bs, ys, probs = [], [], [], [], []
+    for i, sh in enumerate(shapes):
+        x, w, b, _ = make_inputs(sh, 1000 + i)
+        xs.append(x.bfloat16().to(dev))
+        ws.append(w.bfloat16().to(dev))
+        bs.append(b.to(dev))
+        ys.append(torch.empty(sh.y_shape(), dtype=torch.bfloat16, device=dev))
+        probs.append(B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, 1,
+                               B.GBCONV_BF16, B.GBCONV_BF16, B.GBCONV_NHWC,
+                               B.GBCONV_FLAG_BIAS | B.GBCONV_FLAG_RELU))
+    flops = sum(s.flops for s in shapes)
+    xp = [t.data_ptr() for t in xs]
+    wp = [t.data_ptr() for t in ws]
+    bp = [t.data_ptr() for t in bs]
+    yp = [t.data_ptr() for t in ys]
+
+    def grouped(i, stream):
+        B.check(B.conv2d_grouped(len(probs), probs, xp, wp, bp, yp, 0, 0, stream), "grouped")
+
+    def separate(i, stream):
+        for k, p in enumerate(probs):
+            B.check(B.conv2d_fwd(p, xp[k], wp[k], bp[k], 0, 0, yp[k], 0, 0, stream), "fwd")
+
+    class L:
+        def __init__(s, f):
+            s.launch = f
+
+    steps = max(3, min(args.steps, 10))
+    rg = bench_layers([L(grouped)], steps, 3, 1, torch, dist_on)
+    rs = bench_layers([L(separate)], steps, 3, 1, torch, dist_on)
+    del xs, ws, ys
+    torch.cuda.empty_cache()
+    return {"problems": len(shapes), "tflop_per_step": round(flops / 1e12, 4),
+            "grouped_ms": round(rg["ms_per_step"], 4),
+            "grouped_tflops": round(flops / (rg["ms_per_step"] * 1e-3) / 1e12, 1),
+            "separate_launches_ms": round(rs["ms_per_step"], 4),
+            "separate_launches_tflops": round(flops / (rs["ms_per_step"] * 1e-3) / 1e12, 1),
+            "both_in_cuda_graphs": True,
+            "frac_of_bf16_peak": round(flops / (rg["ms_per_step"] * 1e-3) / 1e12 / pk["bf16_tflops"], 4)}
+
+
+def bench_backward(torch, dev, args, dist_on, pk):
+    from paper_2207_00257_gb300 import binding as B
+    from paper_2207_00257_gb300.synth import config_backward, make_inputs
+    sh = config_backward()
+    x, w, b, g = make_inputs(sh, 5, grad=True)
+    xb, wb, gb = x.bfloat16().to(dev), w.bfloat16().to(dev), g.bfloat16().to(dev)
+    dx = torch.empty(sh.x_shape(), dtype=torch.bfloat16, device=dev)
+    dw = torch.empty(sh.w_shape(), dtype=torch.float32, device=dev)
+    db = torch.empty(sh.K, dtype=torch.float32, device=dev)
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                     B.GBCONV_BF16, B.GBCONV_BF16, B.GBCONV_NHWC, 0)
+    s1, nd = B.gbconv_workspace_size(B.GBCONV_OP_DGRAD, prob)
+    s2, nw = B.gbconv_workspace_size(B.GBCONV_OP_WGRAD, prob)
+    wsd = torch.empty(max(nd, 1), dtype=torch.uint8, device=dev)
+    wsw = torch.empty(max(nw, 1), dtype=torch.uint8, device=dev)
+
+    def dgrad(i, stream):
+        B.check(B.conv2d_dgrad(prob, gb.data_ptr(), wb.data_ptr(), dx.data_ptr(),
+                               wsd.data_ptr(), nd, stream), "dgrad")
+
+    def wgrad(i, stream):
+        B.check(B.conv2d_wgrad(prob, xb.data_ptr(), gb.data_ptr(), dw.data_ptr(), db.data_ptr(),
+                               wsw.data_ptr(), nw, stream), "wgrad")
+
+    class L:
+        def __init__(s, f):
+            s.launch = f
+
+    steps = max(3, min(args.steps, 20))
+    res = bench_layers([L(dgrad), L(wgrad)], steps, 3, 1, torch, dist_on)
+    f = sh.flops
+    return {"workload": sh.tag, "dgrad_us": round(res["launch_us"][0], 1),
+            "wgrad_us": round(res["launch_us"][1], 1),
+            "dgrad_tflops": round(f / (res["launch_us"][0] * 1e-6) / 1e12, 1),
+            "wgrad_tflops": round(f / (res["launch_us"][1] * 1e-6) / 1e12, 1),
+            "wgrad_split_k": B.gbconv_get_config(B.GBCONV_OP_WGRAD, prob)[1].split_k}
+
+
+# ---------------------------------------------------------------------------
+# the FP64 CPU oracle: cpu_baseline leg and the reference arm
+# ---------------------------------------------------------------------------
+def oracle_sample_run(images, nthreads=0):
+    """Runs the oracle on the first `images` images of each ResNet layer
+    (seeded inputs of the bench's buffer set 0). Returns (seconds, flops, outputs)."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2207_00257_gb300.synth import make_inputs, resnet_layers
+    outs, secs, flops = [], 0.0, 0
+    for i, sh in enumerate(resnet_layers(32)):
+        x, w, b, _ = make_inputs(sh, 100 + i)
+        xs = x[:images].bfloat16().double().numpy()
+        wd = w.bfloat16().double().numpy()
+        p = oracle.Conv(images, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                        "NHWC")
+        t = time.perf_counter()
+        y, bound = oracle.conv2d_fwd(p, xs, wd, b.double().numpy(), relu=True,
+                                     nthreads=nthreads, with_bound=True)
+        secs += time.perf_counter() - t
+        flops += p.flops
+        outs.append((y, bound))
+    return secs, flops, outs
+
+
+def cpu_baseline(layers, torch):
+    import numpy as np
+    import oracle
+    images = int(os.environ.get("GBCONV_CPU_SAMPLE_IMAGES", "4"))
+    secs, flops, outs = oracle_sample_run(images)
+    errs = {}
+    # refresh the outputs of buffer set 0 (the oracle's inputs) and compare
+    stream = torch.cuda.current_stream().cuda_stream
+    for lay in layers:
+        lay.launch(0, stream)
+    torch.cuda.synchronize()
+    for lay, (y, bound) in zip(layers, outs):
+        got = lay.ys[0][:images].double().cpu().numpy()
+        errs[lay.sh.tag] = float(f"{oracle.max_normalised_error(got, y, bound):.3e}")
+    return {"value": round(flops / secs / 1e12, 6), "unit": "TFLOP/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"first {images} of 32 images of each of the 4 layers "
+                      f"({flops / 1e9:.2f} GFLOP, FP64 six-loop, all host threads)",
+            "seconds": round(secs, 2),
+            "max_normalised_err_bf16_vs_oracle": errs}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    images = 1
+    for _ in range(args.warmup):
+        oracle_sample_run(images)
+    secs, flops = 0.0, 0
+    for _ in range(args.steps):
+        s, f, _ = oracle_sample_run(images)
+        secs += s
+        flops += f
+    value = flops / secs / 1e12
+    out = {"impl": "reference", "metric": "conv2d TFLOP/s & % of tensor peak, BF16/FP8 vs FP32 at stated rel err",
+           "value": round(value, 6), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "resnet50_bottleneck_layers_bf16_nhwc_batch32",
+                                           "sample_per_step": f"{images} of 32 images per layer"},
+           "cpu_baseline": {"value": round(value, 6), "unit": "TFLOP/s", "cores": os.cpu_count(),
+                            "kind": "oracle",
+                            "sample": f"first {images} image(s) of each of the 4 layers per step"},
+           "e2e": {"value": round(value, 6), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

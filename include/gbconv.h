@@ -1,0 +1,212 @@
+/*
+ * gbconv.h -- C ABI of a GB300 (sm_103a) dense 2D convolution library.
+ *
+ * The operation is the convolution that the paper (arXiv 2207.00257) names as
+ * the critical kernel of its PyTorch case: Sec. 1 and Sec. 5.A (PyTorch's
+ * native CPU backend computes 2D convolution as six nested loops) and Sec. 5.B
+ * (the forward and backward passes of ResNet-50's convolutional layers, done
+ * there as im2col + GEMM on NCHW tensors). With stride (u, v), zero padding
+ * (ph, pw) and dilation (dh, dw):
+ *
+ *   P = floor((H + 2*ph - dh*(R-1) - 1) / u) + 1,  Q likewise with W, pw, dw, S, v
+ *   y[n,k,p,q] = b[k] + sum_{c,r,s} x[n,c, p*u + r*dh - ph, q*v + s*dw - pw] * w[k,c,r,s]
+ *
+ * (cross-correlation; x outside the image reads as 0), optionally followed by
+ * ReLU. For the loss L = sum g*y the backward entry points compute
+ *
+ *   dx[n,c,h,w] = sum over (k,r,s,p,q) with p*u+r*dh-ph = h, q*v+s*dw-pw = w of g[n,k,p,q]*w[k,c,r,s]
+ *   dw[k,c,r,s] = sum_{n,p,q} g[n,k,p,q] * x[n,c,p*u+r*dh-ph, q*v+s*dw-pw]
+ *   db[k]       = sum_{n,p,q} g[n,k,p,q]
+ *
+ * Layouts. GBCONV_NHWC: x[n][h][w][c], filters w[k][r][s][c] (KRSC), y and g
+ * y[n][p][q][k]. GBCONV_NCHW: x[n][c][h][w], filters w[k][c][r][s] (KCRS), y and
+ * g y[n][k][p][q]. All tensors are dense and contiguous in that order.
+ *
+ * Ownership. The caller owns every tensor and every workspace; all tensor and
+ * workspace pointers are DEVICE pointers unless a comment says "host". The
+ * library owns only small host-side caches (tensor maps, tuning table) and one
+ * static device error word. No entry point allocates device memory.
+ *
+ * Asynchrony and errors. Compute entry points validate their arguments on the
+ * host, enqueue work on `stream` and return without synchronising. Their
+ * status covers validation and launch errors only: on any error nothing is
+ * launched. Every wait inside a kernel is bounded; a wait that runs out sets
+ * the device error word and the kernel exits early. gbconv_get_device_error()
+ * synchronises the stream and reports (and clears) that word. Entry points are
+ * thread-safe (caches are mutex-guarded); calls that overlap on the GPU and
+ * write the same output or workspace race, as with any CUDA kernel.
+ */
+#ifndef GBCONV_H
+#define GBCONV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBCONV_OK = 0,
+    GBCONV_ERR_INVALID_ARG = 1,   /* null pointer, non-positive size, bad enum, P or Q < 1 */
+    GBCONV_ERR_UNSUPPORTED = 2,   /* valid convolution this entry point does not implement */
+    GBCONV_ERR_ALIGNMENT = 3,     /* channel count or pointer misses the 16-byte rule of TMA */
+    GBCONV_ERR_WORKSPACE = 4,     /* workspace smaller than gbconv_workspace_size() */
+    GBCONV_ERR_CUDA = 5,          /* a CUDA runtime or driver call failed */
+    GBCONV_ERR_TIMEOUT = 6        /* a bounded in-kernel wait ran out */
+} gbconv_status_t;
+
+typedef enum { GBCONV_F32 = 0, GBCONV_BF16 = 1, GBCONV_E4M3 = 2 } gbconv_dtype_t;
+typedef enum { GBCONV_NCHW = 0, GBCONV_NHWC = 1 } gbconv_layout_t;
+typedef enum { GBCONV_OP_FWD = 0, GBCONV_OP_DGRAD = 1, GBCONV_OP_WGRAD = 2 } gbconv_op_t;
+
+#define GBCONV_FLAG_BIAS 1u   /* add b[k] (fp32 for F32 output, else fp32 as well) */
+#define GBCONV_FLAG_RELU 2u   /* y = max(y, 0) after the bias */
+
+/* One convolution. Sizes are element counts. in_dtype is the type of x and w
+ * (and of g for the backward entry points); out_dtype is the type of y (or
+ * dx). Supported combinations:
+ *   F32  -> F32   NCHW or NHWC, any stride/pad/dilation (CUDA-core FFMA kernel)
+ *   BF16 -> BF16 or F32   NHWC, C % 8 == 0, K % 8 == 0 (tensor cores, FP32 accumulate)
+ *   E4M3 -> BF16  NHWC, C % 16 == 0, K % 8 == 0 (tensor cores, FP32 accumulate,
+ *                 y = b + x_scale * w_scale[k] * sum(xq * wq))
+ * Padding must be in [0, 127] and dilation*(R-1) <= 127 (the im2col TMA range). */
+typedef struct {
+    int32_t N, C, H, W, K, R, S;
+    int32_t stride_h, stride_w;
+    int32_t pad_h, pad_w;
+    int32_t dil_h, dil_w;
+    int32_t in_dtype;   /* gbconv_dtype_t */
+    int32_t out_dtype;  /* gbconv_dtype_t */
+    int32_t layout;     /* gbconv_layout_t */
+    uint32_t flags;     /* GBCONV_FLAG_* */
+} gbconv_problem_t;
+
+/* Launch configuration of one convolution (chosen by the autotuner or set by
+ * hand). block_n: output-channel tile (32..256, tensor-core paths) ; stages:
+ * shared-memory pipeline depth; split_k: number of slices the reduction is
+ * cut into (wgrad); raster: 0 = output-channel tiles fastest, 1 = pixel tiles
+ * fastest. A zero field means "library default". */
+typedef struct {
+    int32_t block_n;
+    int32_t stages;
+    int32_t split_k;
+    int32_t raster;
+} gbconv_config_t;
+
+/* A CUDA stream (cudaStream_t). NULL means the legacy default stream. */
+typedef void *gbconv_stream_t;
+
+/* Output spatial size P, Q of the formula above. Host only, no GPU use.
+ * Returns GBCONV_ERR_INVALID_ARG for invalid problems (P or Q < 1, sizes < 1,
+ * negative padding, stride or dilation < 1). */
+gbconv_status_t gbconv_output_dims(const gbconv_problem_t *prob, int32_t *P, int32_t *Q);
+
+/* Bytes of device workspace `op` needs for `prob` (0 when none). Host only.
+ * FWD: 0. DGRAD: the filter rotated by 180 degrees with C and K exchanged
+ * (tensor-core path, stride 1), rounded up to 256 bytes; 0 otherwise.
+ * WGRAD: split_k * (K*R*S*C + K) fp32 partial sums, rounded up to 256 bytes. */
+gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, size_t *bytes);
+
+/* Forward convolution (paper Sec. 5.B, forward pass of a convolutional layer).
+ *   x [N,H,W,C] (NHWC) or [N,C,H,W] (NCHW), in_dtype
+ *   w [K,R,S,C] (NHWC) or [K,C,R,S] (NCHW), in_dtype
+ *   bias [K] fp32, read when GBCONV_FLAG_BIAS is set (may be NULL otherwise)
+ *   x_scale: device pointer to one fp32 (E4M3 only, else ignored)
+ *   w_scale: device pointer to K fp32 (E4M3 only, else ignored)
+ *   y [N,P,Q,K] (NHWC) or [N,K,P,Q] (NCHW), out_dtype; must not alias x or w
+ *   ws / ws_bytes: workspace (none needed; may be NULL / 0)
+ * Tensor-core paths require x, w, y 16-byte aligned. */
+gbconv_status_t conv2d_fwd(const gbconv_problem_t *prob, const void *x, const void *w,
+                           const float *bias, const float *x_scale, const float *w_scale,
+                           void *y, void *ws, size_t ws_bytes, gbconv_stream_t stream);
+
+/* Data gradient (paper Sec. 5.B, backward pass; the transposed convolution).
+ *   dy [N,P,Q,K] or [N,K,P,Q] (in_dtype), w as in conv2d_fwd (in_dtype),
+ *   dx [N,H,W,C] or [N,C,H,W] (out_dtype). dx is fully overwritten.
+ * BF16 NHWC with stride 1 and pad <= dil*(R-1) runs on the tensor cores as a
+ * forward convolution of dy with the rotated filter (needs the workspace);
+ * everything else runs on a CUDA-core gather kernel with FP32 accumulation. */
+gbconv_status_t conv2d_dgrad(const gbconv_problem_t *prob, const void *dy, const void *w,
+                             void *dx, void *ws, size_t ws_bytes, gbconv_stream_t stream);
+
+/* Weight and bias gradient (paper Sec. 5.B, backward pass).
+ *   x as in conv2d_fwd, dy as in conv2d_dgrad (both in_dtype)
+ *   dw [K,R,S,C] or [K,C,R,S] fp32, fully overwritten
+ *   db [K] fp32 or NULL (then not computed)
+ * The reduction over N*P*Q is cut into split_k slices whose fp32 partial sums
+ * go to the workspace; a second kernel adds the slices in a fixed order with
+ * compensated (Neumaier) summation, so results are deterministic. */
+gbconv_status_t conv2d_wgrad(const gbconv_problem_t *prob, const void *x, const void *dy,
+                             float *dw, float *db, void *ws, size_t ws_bytes,
+                             gbconv_stream_t stream);
+
+/* Many independent forward convolutions in ONE persistent launch.
+ *   probs: HOST array of `count` problems (1 <= count <= 64 per launch; larger
+ *          counts are split into launches of 64), all BF16 -> BF16 NHWC.
+ *   x, w, bias, y: HOST arrays of `count` DEVICE pointers (bias entries may be
+ *          NULL when the problem has no GBCONV_FLAG_BIAS).
+ * All per-problem descriptors travel as kernel parameters, so the call makes
+ * no host-to-device copy and can be captured in a CUDA graph. Tile configs
+ * come from the tuning table (gbconv_tune) or the built-in heuristic. */
+gbconv_status_t conv2d_grouped(int32_t count, const gbconv_problem_t *probs,
+                               const void *const *x, const void *const *w,
+                               const float *const *bias, void *const *y, void *ws,
+                               size_t ws_bytes, gbconv_stream_t stream);
+
+/* FP8 operand preparation for the E4M3 forward path. `in` holds `rows`
+ * contiguous groups of `len` values (in_dtype F32 or BF16). Per group,
+ * entirely in binary32:
+ *   scale[r] = max(max_i |in[r,i]| / 448, 1e-12)
+ *   out[r,i] = E4M3(in[r,i] / scale[r]), round to nearest even, saturating to +-448
+ * rows = 1 gives the per-tensor activation scale; rows = K over a KRSC filter
+ * gives per-output-channel weight scales. out (uint8 codes) and scale are
+ * device pointers; no workspace. */
+gbconv_status_t gbconv_quantize_e4m3(const void *in, int32_t in_dtype, int64_t rows, int64_t len,
+                                     uint8_t *out, float *scale, gbconv_stream_t stream);
+
+/* Tuning. gbconv_get_config returns the config `op` would use for `prob`
+ * (tuned entry if present, else the heuristic); gbconv_set_config stores one.
+ * gbconv_tune times every candidate config on the caller's buffers (same
+ * arguments as the op: FWD a=x, b=w, out=y; DGRAD a=dy, b=w, out=dx; WGRAD
+ * a=x, b=dy, out=dw) with `reps` launches each on `stream`, stores and returns
+ * the fastest. The table is keyed by problem, op and device name and can be
+ * saved to / loaded from a JSON file (host path). */
+gbconv_status_t gbconv_get_config(int32_t op, const gbconv_problem_t *prob, gbconv_config_t *cfg);
+gbconv_status_t gbconv_set_config(int32_t op, const gbconv_problem_t *prob,
+                                  const gbconv_config_t *cfg);
+gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void *a,
+                            const void *b, const float *bias, void *out, void *ws,
+                            size_t ws_bytes, int32_t reps, gbconv_stream_t stream,
+                            gbconv_config_t *best);
+gbconv_status_t gbconv_tune_cache_save(const char *path);
+gbconv_status_t gbconv_tune_cache_load(const char *path);
+
+/* Synchronises `stream`, then returns GBCONV_ERR_TIMEOUT if a bounded wait in
+ * any kernel ran out since the last call (and clears the word), GBCONV_ERR_CUDA
+ * if the synchronisation failed, else GBCONV_OK. */
+gbconv_status_t gbconv_get_device_error(gbconv_stream_t stream);
+
+/* Static, human-readable name of a status. Never NULL. */
+const char *gbconv_status_string(gbconv_status_t status);
+
+/* Test and diagnosis controls (not needed in normal use):
+ *   GBCONV_DEBUG_WAIT_LIMIT_NS: time limit of every in-kernel wait (default
+ *       2e9 ns; 0 restores the default);
+ *   GBCONV_DEBUG_SKIP_LOADS: when 1, tensor-core kernels issue no loads, so
+ *       their consumers' waits run out and the kernel reports a timeout. */
+#define GBCONV_DEBUG_WAIT_LIMIT_NS 1
+#define GBCONV_DEBUG_SKIP_LOADS 2
+gbconv_status_t gbconv_debug_set(int32_t key, int64_t value);
+
+/* Library version, as major*10000 + minor*100 + patch. */
+int32_t gbconv_version(void);
+
+/* Frees host-side caches (tensor maps, tuning table). Safe to call twice. */
+void gbconv_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBCONV_H */

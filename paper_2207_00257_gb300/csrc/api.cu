@@ -1,0 +1,591 @@
+// api.cu -- the C ABI of include/gbconv.h: argument validation, dispatch to
+// the CUDA-core and tensor-core kernels, the device error word, and the
+// tuning table (in memory, JSON on disk).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+// The one device word every bounded in-kernel wait reports to (static device
+// memory: nothing is allocated for it).
+__device__ unsigned int g_gbconv_error_word;
+
+namespace gbc {
+namespace {
+
+std::mutex g_mu;
+uint64_t g_wait_ns = 2000000000ull;
+int g_skip_loads = 0;
+
+struct DevInfo {
+    unsigned int *err = nullptr;
+    int sms = 0;
+    std::string name;
+    bool init = false;
+};
+constexpr int MAX_DEV = 64;
+DevInfo g_dev[MAX_DEV];
+
+DevInfo *dev_info() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return nullptr;
+    std::lock_guard<std::mutex> lock(g_mu);
+    DevInfo &di = g_dev[dev];
+    if (!di.init) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_gbconv_error_word) != cudaSuccess) return nullptr;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return nullptr;
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return nullptr;
+        di.err = static_cast<unsigned int *>(p);
+        di.sms = sms;
+        di.name = prop.name;
+        di.init = true;
+    }
+    return &di;
+}
+
+// ---- tuning table ----
+std::map<std::string, TcConfig> g_tune;
+
+std::string problem_key(int op, const gbconv_problem_t &p) {
+    DevInfo *di = dev_info();
+    char buf[512];
+    snprintf(buf, sizeof buf, "%d|%d,%d,%d,%d,%d,%d,%d|%d,%d,%d,%d,%d,%d|%d,%d,%d,%u|%s", op, p.N,
+             p.C, p.H, p.W, p.K, p.R, p.S, p.stride_h, p.stride_w, p.pad_h, p.pad_w, p.dil_h,
+             p.dil_w, p.in_dtype, p.out_dtype, p.layout, p.flags, di ? di->name.c_str() : "?");
+    return buf;
+}
+
+bool tuned(int op, const gbconv_problem_t &p, TcConfig *out) {
+    std::string k = problem_key(op, p);
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_tune.find(k);
+    if (it == g_tune.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+// ---- validation ----
+gbconv_status_t make_dims(const gbconv_problem_t *p, Dims *d) {
+    if (!p) return GBCONV_ERR_INVALID_ARG;
+    if (p->N < 0 || p->C < 1 || p->H < 1 || p->W < 1 || p->K < 1 || p->R < 1 || p->S < 1)
+        return GBCONV_ERR_INVALID_ARG;
+    if (p->stride_h < 1 || p->stride_w < 1 || p->dil_h < 1 || p->dil_w < 1 || p->pad_h < 0 ||
+        p->pad_w < 0)
+        return GBCONV_ERR_INVALID_ARG;
+    if (p->in_dtype < GBCONV_F32 || p->in_dtype > GBCONV_E4M3 || p->out_dtype < GBCONV_F32 ||
+        p->out_dtype > GBCONV_E4M3 || (p->layout != GBCONV_NCHW && p->layout != GBCONV_NHWC))
+        return GBCONV_ERR_INVALID_ARG;
+    if (p->flags & ~(GBCONV_FLAG_BIAS | GBCONV_FLAG_RELU)) return GBCONV_ERR_INVALID_ARG;
+    long long pn = (long long)p->H + 2ll * p->pad_h - (long long)p->dil_h * (p->R - 1) - 1;
+    long long qn = (long long)p->W + 2ll * p->pad_w - (long long)p->dil_w * (p->S - 1) - 1;
+    if (pn < 0 || qn < 0) return GBCONV_ERR_INVALID_ARG;
+    d->N = p->N;
+    d->C = p->C;
+    d->H = p->H;
+    d->W = p->W;
+    d->K = p->K;
+    d->R = p->R;
+    d->S = p->S;
+    d->P = (int)(pn / p->stride_h + 1);
+    d->Q = (int)(qn / p->stride_w + 1);
+    d->u = p->stride_h;
+    d->v = p->stride_w;
+    d->ph = p->pad_h;
+    d->pw = p->pad_w;
+    d->dh = p->dil_h;
+    d->dw = p->dil_w;
+    d->layout = p->layout;
+    d->in_dtype = p->in_dtype;
+    d->out_dtype = p->out_dtype;
+    d->flags = p->flags;
+    // element counts must fit the kernels' 64-bit offsets comfortably
+    const long long lim = 1ll << 40;
+    if ((long long)d->N * d->C * d->H * d->W >= lim || (long long)d->N * d->K * d->P * d->Q >= lim ||
+        (long long)d->K * d->C * d->R * d->S >= lim)
+        return GBCONV_ERR_INVALID_ARG;
+    return GBCONV_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+
+// Tensor-core forward eligibility beyond tc_fwd_supported: argument-level checks.
+gbconv_status_t check_tc_fwd(const Dims &d, const void *x, const void *w, const void *y) {
+    if (d.in_dtype == GBCONV_BF16 && (d.C % 8 || d.K % 8)) return GBCONV_ERR_ALIGNMENT;
+    if (d.in_dtype == GBCONV_E4M3 && (d.C % 16 || d.K % 8)) return GBCONV_ERR_ALIGNMENT;
+    if (!aligned16(x) || !aligned16(w) || !aligned16(y)) return GBCONV_ERR_ALIGNMENT;
+    if (!tc_fwd_supported(d)) return GBCONV_ERR_UNSUPPORTED;
+    return GBCONV_OK;
+}
+
+// The data gradient of a stride-1 convolution is a forward convolution of dy
+// with the filter rotated by 180 degrees (C and K exchanged) and padding
+// dil*(R-1) - pad: dx[n,h,w,c] = sum_{k,r',s'} dy[n, h - (pad' ) + r' d, ...] w_rot.
+bool dgrad_as_fwd(const Dims &d, Dims *t) {
+    if (d.layout != GBCONV_NHWC || d.in_dtype != GBCONV_BF16) return false;
+    if (d.u != 1 || d.v != 1) return false;
+    const int ph2 = d.dh * (d.R - 1) - d.ph, pw2 = d.dw * (d.S - 1) - d.pw;
+    if (ph2 < 0 || pw2 < 0) return false;
+    Dims e = d;
+    e.C = d.K;
+    e.K = d.C;
+    e.H = d.P;
+    e.W = d.Q;
+    e.ph = ph2;
+    e.pw = pw2;
+    e.P = d.H;
+    e.Q = d.W;
+    e.flags = 0;
+    e.in_dtype = GBCONV_BF16;
+    e.out_dtype = d.out_dtype;
+    if (e.C % 8 || e.K % 8 || !tc_fwd_supported(e)) return false;
+    *t = e;
+    return true;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+int wgrad_default_slices(const Dims &d) {
+    // about eight CTAs per SM of a 152-SM part, at most 64 slices, and no
+    // more slices than the reduction has 16-pixel runs
+    long long tiles = (long long)((d.K + 127) / 128) * ((d.C + 63) / 64) * d.R * d.S;
+    long long runs = (long long)d.N * d.P * ((d.Q + 15) / 16);
+    long long s = (1216 + tiles - 1) / tiles;
+    s = std::min<long long>(s, 64);
+    s = std::min<long long>(s, std::max<long long>(runs, 1));
+    return (int)std::max<long long>(s, 1);
+}
+
+TcConfig config_for(int op, const gbconv_problem_t &p, const Dims &d) {
+    TcConfig c{};
+    if (tuned(op, p, &c)) return c;
+    if (op == GBCONV_OP_WGRAD) {
+        if (tc_wgrad_supported(d)) return tc_wgrad_default_config(d);
+        c.split_k = wgrad_default_slices(d);
+        return c;
+    }
+    if (op == GBCONV_OP_DGRAD) {
+        Dims t;
+        if (dgrad_as_fwd(d, &t)) return tc_fwd_default_config(t);
+        return c;
+    }
+    if (tc_fwd_supported(d)) return tc_fwd_default_config(d);
+    return c;
+}
+
+size_t wgrad_ws_bytes(const Dims &d, int slices) {
+    size_t kcrs = (size_t)d.K * d.C * d.R * d.S;
+    return round256((size_t)slices * (kcrs + (size_t)d.K) * sizeof(float));
+}
+
+gbconv_status_t do_fwd(const Dims &d, const TcConfig &cfg, const void *x, const void *w,
+                       const float *bias, const float *x_scale, const float *w_scale, void *y,
+                       cudaStream_t st) {
+    if (d.M() == 0) return GBCONV_OK;
+    if (d.in_dtype == GBCONV_F32) {
+        if (d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
+        return launch_simt_fwd(d, x, w, bias, y, st);
+    }
+    if (d.layout != GBCONV_NHWC) return GBCONV_ERR_UNSUPPORTED;
+    if (d.in_dtype == GBCONV_E4M3 && (!x_scale || !w_scale)) return GBCONV_ERR_INVALID_ARG;
+    gbconv_status_t s = check_tc_fwd(d, x, w, y);
+    if (s != GBCONV_OK) return s;
+    return launch_tc_fwd(d, cfg, x, w, bias, x_scale, w_scale, y, st);
+}
+
+gbconv_status_t do_dgrad(const Dims &d, const TcConfig &cfg, const void *dy, const void *w,
+                         void *dx, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if ((long long)d.N * d.H * d.W == 0) return GBCONV_OK;
+    if (d.in_dtype == GBCONV_E4M3 || d.out_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
+    if (d.in_dtype == GBCONV_F32 && d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
+    Dims t;
+    if (dgrad_as_fwd(d, &t)) {
+        size_t need = round256((size_t)d.K * d.R * d.S * d.C * 2);
+        if (!ws || ws_bytes < need) return GBCONV_ERR_WORKSPACE;
+        if (!aligned16(ws) || !aligned16(dy) || !aligned16(dx)) return GBCONV_ERR_ALIGNMENT;
+        gbconv_status_t s = launch_rotate_filter(d, w, ws, st);
+        if (s != GBCONV_OK) return s;
+        return launch_tc_fwd(t, cfg, dy, ws, nullptr, nullptr, nullptr, dx, st);
+    }
+    return launch_simt_dgrad(d, dy, w, dx, st);
+}
+
+gbconv_status_t do_wgrad(const Dims &d, const TcConfig &cfg, const void *x, const void *dy,
+                         float *dw, float *db, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (d.in_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
+    const long long kcrs = (long long)d.K * d.C * d.R * d.S;
+    const int slices = std::max(1, cfg.split_k);
+    if (slices > 1024) return GBCONV_ERR_INVALID_ARG;
+    size_t need = wgrad_ws_bytes(d, slices);
+    if (!ws || ws_bytes < need) return GBCONV_ERR_WORKSPACE;
+    float *part = static_cast<float *>(ws);
+    float *bpart = part + (size_t)slices * kcrs;
+    if (d.M() == 0) {
+        cudaError_t e = cudaMemsetAsync(dw, 0, kcrs * sizeof(float), st);
+        if (e == cudaSuccess && db) e = cudaMemsetAsync(db, 0, d.K * sizeof(float), st);
+        return cuda_status(e);
+    }
+    gbconv_status_t s;
+    if (tc_wgrad_supported(d) && aligned16(x) && aligned16(dy))
+        s = launch_tc_wgrad_partials(d, cfg, x, dy, part, st);
+    else
+        s = launch_simt_wgrad_partials(d, x, dy, part, slices, st);
+    if (s != GBCONV_OK) return s;
+    s = launch_reduce_slices(part, slices, kcrs, dw, st);
+    if (s != GBCONV_OK) return s;
+    if (db) {
+        int bs = std::min(slices, 64);
+        s = launch_bias_grad(d, dy, db, bpart, bs, st);
+    }
+    return s;
+}
+
+}  // namespace
+
+gbconv_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? GBCONV_OK : GBCONV_ERR_CUDA; }
+
+Guard make_guard() {
+    DevInfo *di = dev_info();
+    Guard g;
+    g.err = di ? di->err : nullptr;
+    g.wait_ns = g_wait_ns;
+    g.skip_loads = g_skip_loads;
+    return g;
+}
+
+int sm_count() {
+    DevInfo *di = dev_info();
+    return di && di->sms > 0 ? di->sms : 1;
+}
+
+}  // namespace gbc
+
+using namespace gbc;
+
+extern "C" {
+
+gbconv_status_t gbconv_output_dims(const gbconv_problem_t *prob, int32_t *P, int32_t *Q) {
+    Dims d;
+    gbconv_status_t s = make_dims(prob, &d);
+    if (s != GBCONV_OK) return s;
+    if (!P || !Q) return GBCONV_ERR_INVALID_ARG;
+    *P = d.P;
+    *Q = d.Q;
+    return GBCONV_OK;
+}
+
+gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, size_t *bytes) {
+    Dims d;
+    gbconv_status_t s = make_dims(prob, &d);
+    if (s != GBCONV_OK) return s;
+    if (!bytes) return GBCONV_ERR_INVALID_ARG;
+    *bytes = 0;
+    if (op == GBCONV_OP_FWD) return GBCONV_OK;
+    if (op == GBCONV_OP_DGRAD) {
+        Dims t;
+        if (dgrad_as_fwd(d, &t)) *bytes = round256((size_t)d.K * d.R * d.S * d.C * 2);
+        return GBCONV_OK;
+    }
+    if (op == GBCONV_OP_WGRAD) {
+        TcConfig c = config_for(op, *prob, d);
+        *bytes = wgrad_ws_bytes(d, std::max(1, c.split_k));
+        return GBCONV_OK;
+    }
+    return GBCONV_ERR_INVALID_ARG;
+}
+
+gbconv_status_t conv2d_fwd(const gbconv_problem_t *prob, const void *x, const void *w,
+                           const float *bias, const float *x_scale, const float *w_scale, void *y,
+                           void *ws, size_t ws_bytes, gbconv_stream_t stream) {
+    (void)ws;
+    (void)ws_bytes;
+    Dims d;
+    gbconv_status_t s = make_dims(prob, &d);
+    if (s != GBCONV_OK) return s;
+    if (!x || !w || !y || ((d.flags & GBCONV_FLAG_BIAS) && !bias)) return GBCONV_ERR_INVALID_ARG;
+    if (x == y || w == y) return GBCONV_ERR_INVALID_ARG;
+    return do_fwd(d, config_for(GBCONV_OP_FWD, *prob, d), x, w, bias, x_scale, w_scale, y,
+                  static_cast<cudaStream_t>(stream));
+}
+
+gbconv_status_t conv2d_dgrad(const gbconv_problem_t *prob, const void *dy, const void *w,
+                             void *dx, void *ws, size_t ws_bytes, gbconv_stream_t stream) {
+    Dims d;
+    gbconv_status_t s = make_dims(prob, &d);
+    if (s != GBCONV_OK) return s;
+    if (!dy || !w || !dx || dx == dy || dx == w) return GBCONV_ERR_INVALID_ARG;
+    return do_dgrad(d, config_for(GBCONV_OP_DGRAD, *prob, d), dy, w, dx, ws, ws_bytes,
+                    static_cast<cudaStream_t>(stream));
+}
+
+gbconv_status_t conv2d_wgrad(const gbconv_problem_t *prob, const void *x, const void *dy,
+                             float *dw, float *db, void *ws, size_t ws_bytes,
+                             gbconv_stream_t stream) {
+    Dims d;
+    gbconv_status_t s = make_dims(prob, &d);
+    if (s != GBCONV_OK) return s;
+    if (!x || !dy || !dw) return GBCONV_ERR_INVALID_ARG;
+    return do_wgrad(d, config_for(GBCONV_OP_WGRAD, *prob, d), x, dy, dw, db, ws, ws_bytes,
+                    static_cast<cudaStream_t>(stream));
+}
+
+gbconv_status_t conv2d_grouped(int32_t count, const gbconv_problem_t *probs, const void *const *x,
+                               const void *const *w, const float *const *bias, void *const *y,
+                               void *ws, size_t ws_bytes, gbconv_stream_t stream) {
+    (void)ws;
+    (void)ws_bytes;
+    if (count < 0 || (count > 0 && (!probs || !x || !w || !y))) return GBCONV_ERR_INVALID_ARG;
+    if (count == 0) return GBCONV_OK;
+    std::vector<Dims> d(count);
+    std::vector<TcConfig> cfg(count);
+    std::vector<const float *> b(count);
+    for (int i = 0; i < count; ++i) {
+        gbconv_status_t s = make_dims(&probs[i], &d[i]);
+        if (s != GBCONV_OK) return s;
+        if (d[i].in_dtype != GBCONV_BF16 || d[i].out_dtype != GBCONV_BF16 ||
+            d[i].layout != GBCONV_NHWC)
+            return GBCONV_ERR_UNSUPPORTED;
+        if (!x[i] || !w[i] || !y[i]) return GBCONV_ERR_INVALID_ARG;
+        b[i] = bias ? bias[i] : nullptr;
+        if ((d[i].flags & GBCONV_FLAG_BIAS) && !b[i]) return GBCONV_ERR_INVALID_ARG;
+        s = check_tc_fwd(d[i], x[i], w[i], y[i]);
+        if (s != GBCONV_OK) return s;
+        cfg[i] = config_for(GBCONV_OP_FWD, probs[i], d[i]);
+    }
+    if (make_guard().err == nullptr) return GBCONV_ERR_CUDA;
+    return launch_tc_grouped(count, d.data(), cfg.data(), x, w, b.data(), y,
+                             static_cast<cudaStream_t>(stream));
+}
+
+gbconv_status_t gbconv_quantize_e4m3(const void *in, int32_t in_dtype, int64_t rows, int64_t len,
+                                     uint8_t *out, float *scale, gbconv_stream_t stream) {
+    if (!in || !out || !scale || rows < 1 || len < 1) return GBCONV_ERR_INVALID_ARG;
+    if (in_dtype != GBCONV_F32 && in_dtype != GBCONV_BF16) return GBCONV_ERR_UNSUPPORTED;
+    return launch_quantize_e4m3(in, in_dtype, rows, len, out, scale,
+                                static_cast<cudaStream_t>(stream));
+}
+
+gbconv_status_t gbconv_get_config(int32_t op, const gbconv_problem_t *prob, gbconv_config_t *cfg) {
+    Dims d;
+    gbconv_status_t s = make_dims(prob, &d);
+    if (s != GBCONV_OK) return s;
+    if (!cfg || op < GBCONV_OP_FWD || op > GBCONV_OP_WGRAD) return GBCONV_ERR_INVALID_ARG;
+    TcConfig c = config_for(op, *prob, d);
+    cfg->block_n = c.block_n;
+    cfg->stages = c.stages;
+    cfg->split_k = c.split_k;
+    cfg->raster = c.raster;
+    return GBCONV_OK;
+}
+
+gbconv_status_t gbconv_set_config(int32_t op, const gbconv_problem_t *prob,
+                                  const gbconv_config_t *cfg) {
+    Dims d;
+    gbconv_status_t s = make_dims(prob, &d);
+    if (s != GBCONV_OK) return s;
+    if (!cfg || op < GBCONV_OP_FWD || op > GBCONV_OP_WGRAD) return GBCONV_ERR_INVALID_ARG;
+    if (cfg->block_n && cfg->block_n != 32 && cfg->block_n != 64 && cfg->block_n != 128 &&
+        cfg->block_n != 256)
+        return GBCONV_ERR_INVALID_ARG;
+    if (cfg->split_k < 0 || cfg->split_k > 1024 || cfg->stages < 0 || cfg->raster < 0 ||
+        cfg->raster > 1)
+        return GBCONV_ERR_INVALID_ARG;
+    TcConfig c = config_for(op, *prob, d);  // defaults for zero fields
+    if (cfg->block_n) c.block_n = cfg->block_n;
+    if (cfg->stages) c.stages = cfg->stages;
+    if (cfg->split_k) c.split_k = cfg->split_k;
+    c.raster = cfg->raster;
+    std::string k = problem_key(op, *prob);
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_tune[k] = c;
+    return GBCONV_OK;
+}
+
+gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void *a, const void *b,
+                            const float *bias, void *out, void *ws, size_t ws_bytes, int32_t reps,
+                            gbconv_stream_t stream, gbconv_config_t *best) {
+    Dims d;
+    gbconv_status_t s = make_dims(prob, &d);
+    if (s != GBCONV_OK) return s;
+    if (!a || !b || !out || op < GBCONV_OP_FWD || op > GBCONV_OP_WGRAD) return GBCONV_ERR_INVALID_ARG;
+    if (reps < 1) reps = 1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const TcConfig base = config_for(op, *prob, d);
+    std::vector<TcConfig> cands;
+    if (op == GBCONV_OP_WGRAD) {
+        for (int sk : {1, 2, 4, 8, 16, 32, 64}) {
+            TcConfig c = base;
+            c.split_k = sk;
+            if (wgrad_ws_bytes(d, sk) <= ws_bytes) cands.push_back(c);
+        }
+    } else {
+        Dims t = d;
+        bool tc = op == GBCONV_OP_FWD ? tc_fwd_supported(d) : dgrad_as_fwd(d, &t);
+        const int kout = op == GBCONV_OP_FWD ? d.K : d.C;
+        if (tc) {
+            for (int bn : {32, 64, 128, 256}) {
+                if (bn > 32 && bn / 2 >= kout) continue;  // wider than needed
+                for (int raster : {0, 1}) {
+                    TcConfig c = base;
+                    c.block_n = bn;
+                    c.stages = 0;  // maximum for this width
+                    c.raster = raster;
+                    cands.push_back(c);
+                }
+            }
+        } else {
+            cands.push_back(base);
+        }
+    }
+    if (cands.empty()) return GBCONV_ERR_WORKSPACE;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return GBCONV_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return GBCONV_ERR_CUDA;
+    }
+    float best_ms = 1e30f;
+    TcConfig best_c = base;
+    for (const TcConfig &c : cands) {
+        auto run = [&]() -> gbconv_status_t {
+            if (op == GBCONV_OP_FWD) return do_fwd(d, c, a, b, bias, nullptr, nullptr, out, st);
+            if (op == GBCONV_OP_DGRAD) return do_dgrad(d, c, a, b, out, ws, ws_bytes, st);
+            return do_wgrad(d, c, a, b, static_cast<float *>(out), nullptr, ws, ws_bytes, st);
+        };
+        if (run() != GBCONV_OK) continue;  // warm-up; skips configs that do not apply
+        cudaEventRecord(e0, st);
+        bool ok = true;
+        for (int i = 0; i < reps && ok; ++i) ok = run() == GBCONV_OK;
+        cudaEventRecord(e1, st);
+        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::string k = problem_key(op, *prob);
+        std::lock_guard<std::mutex> lock(g_mu);
+        g_tune[k] = best_c;
+    }
+    if (best) {
+        best->block_n = best_c.block_n;
+        best->stages = best_c.stages;
+        best->split_k = best_c.split_k;
+        best->raster = best_c.raster;
+    }
+    return gbconv_get_device_error(stream);
+}
+
+gbconv_status_t gbconv_tune_cache_save(const char *path) {
+    if (!path) return GBCONV_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_mu);
+    FILE *f = fopen(path, "w");
+    if (!f) return GBCONV_ERR_INVALID_ARG;
+    fprintf(f, "{\"version\": %d, \"entries\": [\n", 10000);
+    bool first = true;
+    for (auto &kv : g_tune) {
+        fprintf(f, "%s {\"key\": \"%s\", \"block_n\": %d, \"stages\": %d, \"split_k\": %d, \"raster\": %d}",
+                first ? "" : ",\n", kv.first.c_str(), kv.second.block_n, kv.second.stages,
+                kv.second.split_k, kv.second.raster);
+        first = false;
+    }
+    fprintf(f, "\n]}\n");
+    fclose(f);
+    return GBCONV_OK;
+}
+
+// Reads the format written above: one entry object per line.
+gbconv_status_t gbconv_tune_cache_load(const char *path) {
+    if (!path) return GBCONV_ERR_INVALID_ARG;
+    FILE *f = fopen(path, "r");
+    if (!f) return GBCONV_ERR_INVALID_ARG;
+    char line[1024];
+    std::map<std::string, TcConfig> add;
+    while (fgets(line, sizeof line, f)) {
+        const char *k = strstr(line, "\"key\": \"");
+        if (!k) continue;
+        k += 8;
+        const char *ke = strchr(k, '"');
+        if (!ke) continue;
+        TcConfig c{};
+        if (sscanf(ke, "\", \"block_n\": %d, \"stages\": %d, \"split_k\": %d, \"raster\": %d",
+                   &c.block_n, &c.stages, &c.split_k, &c.raster) != 4) {
+            fclose(f);
+            return GBCONV_ERR_INVALID_ARG;
+        }
+        add[std::string(k, ke)] = c;
+    }
+    fclose(f);
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (auto &kv : add) g_tune[kv.first] = kv.second;
+    return GBCONV_OK;
+}
+
+gbconv_status_t gbconv_get_device_error(gbconv_stream_t stream) {
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return GBCONV_ERR_CUDA;
+    DevInfo *di = dev_info();
+    if (!di) return GBCONV_ERR_CUDA;
+    unsigned int h = 0;
+    if (cudaMemcpy(&h, di->err, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return GBCONV_ERR_CUDA;
+    if (h != 0) {
+        unsigned int z = 0;
+        if (cudaMemcpy(di->err, &z, sizeof z, cudaMemcpyHostToDevice) != cudaSuccess)
+            return GBCONV_ERR_CUDA;
+        return GBCONV_ERR_TIMEOUT;
+    }
+    return GBCONV_OK;
+}
+
+const char *gbconv_status_string(gbconv_status_t s) {
+    switch (s) {
+        case GBCONV_OK: return "GBCONV_OK";
+        case GBCONV_ERR_INVALID_ARG: return "GBCONV_ERR_INVALID_ARG";
+        case GBCONV_ERR_UNSUPPORTED: return "GBCONV_ERR_UNSUPPORTED";
+        case GBCONV_ERR_ALIGNMENT: return "GBCONV_ERR_ALIGNMENT";
+        case GBCONV_ERR_WORKSPACE: return "GBCONV_ERR_WORKSPACE";
+        case GBCONV_ERR_CUDA: return "GBCONV_ERR_CUDA";
+        case GBCONV_ERR_TIMEOUT: return "GBCONV_ERR_TIMEOUT";
+    }
+    return "GBCONV_UNKNOWN_STATUS";
+}
+
+gbconv_status_t gbconv_debug_set(int32_t key, int64_t value) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (key == GBCONV_DEBUG_WAIT_LIMIT_NS) {
+        if (value < 0) return GBCONV_ERR_INVALID_ARG;
+        g_wait_ns = value == 0 ? 2000000000ull : (uint64_t)value;
+        return GBCONV_OK;
+    }
+    if (key == GBCONV_DEBUG_SKIP_LOADS) {
+        g_skip_loads = value ? 1 : 0;
+        return GBCONV_OK;
+    }
+    return GBCONV_ERR_INVALID_ARG;
+}
+
+int32_t gbconv_version(void) { return 10000; }
+
+void gbconv_shutdown(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_tune.clear();
+}
+
+}  // extern "C"

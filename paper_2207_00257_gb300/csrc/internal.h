@@ -1,0 +1,84 @@
+// internal.h -- declarations shared by the translation units of libgbconv.
+// Nothing here is part of the public ABI (include/gbconv.h is).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbconv.h"
+
+namespace gbc {
+
+// A validated problem with derived sizes. Stride/pad/dilation per axis:
+// (u, ph, dh) along H and (v, pw, dw) along W.
+struct Dims {
+    int N, C, H, W, K, R, S, P, Q;
+    int u, v, ph, pw, dh, dw;
+    int layout;        // GBCONV_NCHW / GBCONV_NHWC
+    int in_dtype, out_dtype;
+    unsigned flags;
+    long long M() const { return (long long)N * P * Q; }
+};
+
+// Parameters every kernel gets for its bounded waits and error report.
+struct Guard {
+    unsigned int *err;   // device error word (static __device__ variable)
+    uint64_t wait_ns;    // time limit of one wait
+    int skip_loads;      // test control: issue no loads (consumers then time out)
+};
+
+// Error codes written to the device error word.
+enum : unsigned { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1 };
+
+// api.cu
+Guard make_guard();                   // current device's error word + limits
+int sm_count();                       // SMs of the current device
+gbconv_status_t cuda_status(cudaError_t e);
+
+// simt.cu: CUDA-core FP32-accumulate kernels (any layout/stride/dilation).
+gbconv_status_t launch_simt_fwd(const Dims &d, const void *x, const void *w, const float *bias,
+                                void *y, cudaStream_t st);
+gbconv_status_t launch_simt_dgrad(const Dims &d, const void *g, const void *w, void *dx,
+                                  cudaStream_t st);
+// Partial sums of dw per slice: ws[slice][K*C*R*S] in the filter layout.
+gbconv_status_t launch_simt_wgrad_partials(const Dims &d, const void *x, const void *g,
+                                           float *ws, int slices, cudaStream_t st);
+
+// aux.cu
+gbconv_status_t launch_reduce_slices(const float *ws, int slices, long long n, float *out,
+                                     cudaStream_t st);
+gbconv_status_t launch_bias_grad(const Dims &d, const void *g, float *db, float *ws,
+                                 int slices, cudaStream_t st);
+gbconv_status_t launch_rotate_filter(const Dims &d, const void *w, void *w_rot, cudaStream_t st);
+gbconv_status_t launch_quantize_e4m3(const void *in, int in_dtype, long long rows, long long len,
+                                     uint8_t *out, float *scale, cudaStream_t st);
+
+// tc.cu: tensor-core (tcgen05) kernels.
+struct TcConfig {
+    int block_n;   // 32..256, multiple of 32
+    int stages;
+    int split_k;   // wgrad slices
+    int raster;    // 0: output-channel tiles fastest
+};
+bool tc_fwd_supported(const Dims &d);
+TcConfig tc_fwd_default_config(const Dims &d);
+gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg, const void *x, const void *w,
+                              const float *bias, const float *x_scale, const float *w_scale,
+                              void *y, cudaStream_t st);
+gbconv_status_t launch_tc_grouped(int count, const Dims *d, const TcConfig *cfg,
+                                  const void *const *x, const void *const *w,
+                                  const float *const *bias, void *const *y, cudaStream_t st);
+bool tc_wgrad_supported(const Dims &d);
+TcConfig tc_wgrad_default_config(const Dims &d);
+gbconv_status_t launch_tc_wgrad_partials(const Dims &d, const TcConfig &cfg, const void *x,
+                                         const void *g, float *ws, cudaStream_t st);
+
+// tmap.cpp: tensor-map encoding through the driver entry points.
+gbconv_status_t encode_im2col_act(CUtensorMap *m, const Dims &d, const void *x, int elem_bytes,
+                                  int channels_per_pixel, int pixels_per_column);
+gbconv_status_t encode_tiled(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *ptr,
+                             const uint64_t *dims, const uint64_t *strides_bytes,
+                             const uint32_t *box, CUtensorMapSwizzle swz);
+
+}  // namespace gbc

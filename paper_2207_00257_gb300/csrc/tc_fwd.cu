@@ -1,0 +1,538 @@
+// tc_fwd.cu -- tensor-core (tcgen05) implicit-GEMM forward convolution over
+// NHWC, BF16 or FP8-E4M3 operands, FP32 accumulation in Tensor Memory.
+//
+// The forward pass of a convolutional layer (paper Sec. 5.B, which performs
+// it as im2col followed by a GEMM) is computed here as an implicit GEMM:
+//   D[m, k] = sum_{(r,s,c)} A[m, (r,s,c)] * B[k, (r,s,c)]
+// with m = (n, p, q) an output pixel, A the im2col matrix of x (never
+// materialised: a TMA im2col-mode load produces one 128-pixel x 128-byte
+// tile of it per filter tap and channel block) and B the KRSC filter.
+//
+// One persistent CTA per SM walks output tiles of 128 pixels x BN channels.
+// Warp roles (192 threads):
+//   warp 0  producer: one thread issues the TMA loads of A (im2col) and B
+//           (tiled) into an S-stage shared-memory ring ("full"/"empty" mbarriers);
+//   warp 1  MMA issuer: one thread issues tcgen05.mma (128 x BN x 16 for BF16,
+//           x 32 for E4M3) into one of two TMEM accumulators and commits each
+//           stage back to the producer;
+//   warps 2-5 epilogue: tcgen05.ld of the accumulator, FP8 scales, bias,
+//           ReLU, conversion and 16-byte vector stores, while the MMA warp
+//           fills the other accumulator.
+// Every mbarrier wait is bounded (ptx::mbar_wait); on a timeout the kernel
+// records DEVERR_TIMEOUT, drains its own in-flight copies and MMAs, frees
+// TMEM and returns.
+//
+// The same kernel body serves the grouped launch: G problems, each with its
+// own tensor maps and sizes in the kernel parameters, share one tile space.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace gbc {
+namespace {
+
+constexpr int BM = 128;
+constexpr int A_BYTES = BM * 128;  // 128 pixels x 128 bytes of channels
+constexpr int NTHREADS = 192;
+constexpr int SMEM_ALIGN = 1024;
+constexpr int BAR_BYTES = 256;
+constexpr int SMEM_LIMIT = 227 * 1024;
+constexpr int GMAX = 64;  // problems per grouped launch
+
+struct ProbArgs {
+    int M, P, Q;
+    int pw, ph, u, v, dh, dw, S, RS;
+    int c_blocks, kb_per_tile;
+    int n_tiles, bn, K;
+    int relu, out_f32;
+    const float *bias;
+    const float *x_scale;
+    const float *w_scale;
+    void *y;
+};
+
+template <int G>
+struct FwdParams {
+    CUtensorMap tmA[G];
+    CUtensorMap tmB[G];
+    ProbArgs pa[G];
+    int tile_start[G + 1];  // prefix sums of tiles per problem
+    int count;
+    int num_tiles;
+    int stages;
+    int raster;
+    Guard guard;
+};
+
+template <int BN>
+struct TmemCols {
+    static constexpr int v = (2 * BN < 32) ? 32 : 2 * BN;
+};
+
+template <int G>
+__device__ __forceinline__ void decode(const FwdParams<G> &prm, int tile, int &g, int &mt,
+                                       int &nt) {
+    g = 0;
+    if (G > 1) {
+        while (g + 1 < prm.count && tile >= prm.tile_start[g + 1]) ++g;
+    }
+    const int lt = tile - prm.tile_start[g];
+    const int nts = prm.pa[g].n_tiles;
+    if (prm.raster == 0) {
+        mt = lt / nts;
+        nt = lt - mt * nts;
+    } else {
+        const int mts = (prm.pa[g].M + BM - 1) / BM;
+        nt = lt / mts;
+        mt = lt - nt * mts;
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // a -> low half
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+template <int BN, bool FP8, int G>
+__global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_constant__ FwdParams<G> prm) {
+    constexpr int KE = FP8 ? 128 : 64;         // reduction elements per 128-byte row
+    constexpr int KSTEPS = 4;                  // 4 MMAs of 32 bytes of K per row
+    constexpr int TCOLS = TmemCols<BN>::v;
+    constexpr int B_STAGE = BN * 128;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + SMEM_ALIGN - 1) & ~uintptr_t(SMEM_ALIGN - 1));
+    const int stages = prm.stages;
+    uint8_t *sA = base;
+    uint8_t *sB = base + stages * A_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + stages * B_STAGE);
+    uint64_t *full = bars;                // [stages]
+    uint64_t *empty = bars + stages;      // [stages]
+    uint64_t *tfull = bars + 2 * stages;  // [2]
+    uint64_t *tempty = tfull + 2;         // [2]
+    uint64_t *done = tempty + 2;          // [1]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t lim = prm.guard.wait_ns;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < stages; ++i) {
+            ptx::mbar_init(&full[i], 1);
+            ptx::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&tfull[i], 1);
+            ptx::mbar_init(&tempty[i], 4);
+        }
+        ptx::mbar_init(done, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(tmem_slot, TCOLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(prm.guard.err, DEVERR_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------ producer ------------------------------
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < prm.num_tiles; tile += gridDim.x) {
+                int g, mt, nt;
+                decode(prm, tile, g, mt, nt);
+                const ProbArgs &pa = prm.pa[g];
+                const int m0 = mt * BM;
+                const int q = m0 % pa.Q, t = m0 / pa.Q;
+                const int p = t % pa.P, n = t / pa.P;
+                const int wc = q * pa.v - pa.pw, hc = p * pa.u - pa.ph;
+                const int n0 = nt * pa.bn;
+                const CUtensorMap *ta = &prm.tmA[g];
+                const CUtensorMap *tb = &prm.tmB[g];
+                const uint32_t bytes = A_BYTES + pa.bn * 128;
+                int r = 0, s = 0;
+                for (int rs = 0; ok && rs < pa.RS; ++rs) {
+                    for (int cb = 0; cb < pa.c_blocks; ++cb) {
+                        if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort_flag)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        if (!prm.guard.skip_loads) {
+                            ptx::mbar_arrive_expect_tx(&full[stage], bytes);
+                            ptx::tma_load_im2col_4d(sA + stage * A_BYTES, ta, &full[stage],
+                                                    cb * KE, wc, hc, n,
+                                                    (uint16_t)(s * pa.dw), (uint16_t)(r * pa.dh));
+                            ptx::tma_load_3d(sB + stage * B_STAGE, tb, &full[stage], cb * KE, rs,
+                                             n0);
+                            ++issued;
+                        }
+                        if (++stage == stages) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    }
+                    if (++s == pa.S) {
+                        s = 0;
+                        ++r;
+                    }
+                }
+            }
+            // Drain: the last min(issued, stages) fills must have landed before
+            // this CTA's shared memory can be released.
+            int st = stage;
+            uint32_t ph = phase;
+            for (int i = 0; i < min(issued, stages); ++i) {
+                if (st == 0) {
+                    st = stages;
+                    ph ^= 1;
+                }
+                --st;
+                if (!ptx::mbar_wait(&full[st], ph, lim, abort_flag)) {
+                    // give the copy one more full period without the abort shortcut
+                    volatile int zero = 0;
+                    if (!ptx::mbar_wait(&full[st], ph, lim, &zero)) fail();
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------ MMA issuer ----------------------------
+            int stage = 0;
+            uint32_t phase = 0;
+            int local = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < prm.num_tiles; tile += gridDim.x, ++local) {
+                int g, mt, nt;
+                decode(prm, tile, g, mt, nt);
+                const ProbArgs &pa = prm.pa[g];
+                const int acc = local & 1;
+                const uint32_t aph = (local >> 1) & 1;
+                if (!ptx::mbar_wait(&tempty[acc], aph ^ 1, lim, abort_flag)) {
+                    fail();
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+                const uint32_t idesc = FP8 ? ptx::idesc_e4m3(pa.bn) : ptx::idesc_bf16(pa.bn);
+                for (int kb = 0; kb < pa.kb_per_tile; ++kb) {
+                    if (!ptx::mbar_wait(&full[stage], phase, lim, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint64_t ad = ptx::sdesc_kmajor_sw128(ptx::smem_addr(sA + stage * A_BYTES));
+                    const uint64_t bd = ptx::sdesc_kmajor_sw128(ptx::smem_addr(sB + stage * B_STAGE));
+#pragma unroll
+                    for (int k = 0; k < KSTEPS; ++k) {
+                        // +32 bytes of K per step: +2 in the descriptor's address field
+                        if (FP8)
+                            ptx::mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                        else
+                            ptx::mma_f16(d, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0);
+                    }
+                    ptx::mma_commit(&empty[stage]);
+                    if (++stage == stages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) break;
+                ptx::mma_commit(&tfull[acc]);
+            }
+            // Drain: every MMA this thread issued must be complete before TMEM is freed.
+            ptx::mma_commit(done);
+            volatile int zero = 0;
+            if (!ptx::mbar_wait(done, 0, lim, &zero)) fail();
+        }
+    } else {
+        // ------------------------------ epilogue ------------------------------
+        const int quarter = warp & 3;  // TMEM lanes this warp may access
+        const int row = quarter * 32 + lane;
+        int local = 0;
+        for (int tile = blockIdx.x; tile < prm.num_tiles; tile += gridDim.x, ++local) {
+            int g, mt, nt;
+            decode(prm, tile, g, mt, nt);
+            const ProbArgs &pa = prm.pa[g];
+            const int acc = local & 1;
+            const uint32_t aph = (local >> 1) & 1;
+            if (!ptx::mbar_wait(&tfull[acc], aph, lim, abort_flag)) {
+                fail();
+                break;
+            }
+            ptx::tc_fence_after();
+            const long long m = (long long)mt * BM + row;
+            const bool mval = m < pa.M;
+            const float xs = FP8 ? __ldg(pa.x_scale) : 1.f;
+            const int nchunks = pa.bn / 32;
+            for (int j = 0; j < nchunks; ++j) {
+                uint32_t v[32];
+                ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                                            (uint32_t)(acc * BN + j * 32),
+                                        v);
+                ptx::tmem_ld_wait();
+                const int col0 = nt * pa.bn + j * 32;
+                if (!mval || col0 >= pa.K) continue;
+                float f[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    float a = __uint_as_float(v[i]);
+                    const int col = min(col0 + i, pa.K - 1);
+                    if (FP8) a = a * (xs * __ldg(pa.w_scale + col));
+                    if (pa.bias) a = __ldg(pa.bias + col) + a;
+                    if (pa.relu) a = fmaxf(a, 0.f);
+                    f[i] = a;
+                }
+                const bool whole = col0 + 32 <= pa.K;
+                if (pa.out_f32) {
+                    float *yp = reinterpret_cast<float *>(pa.y) + m * pa.K + col0;
+                    if (whole) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            reinterpret_cast<float4 *>(yp)[i] =
+                                make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+                    } else {
+                        for (int i = 0; i < 32 && col0 + i < pa.K; ++i) yp[i] = f[i];
+                    }
+                } else {
+                    __nv_bfloat16 *yp = reinterpret_cast<__nv_bfloat16 *>(pa.y) + m * pa.K + col0;
+                    if (whole) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            reinterpret_cast<uint4 *>(yp)[i] =
+                                make_uint4(pack_bf16(f[8 * i], f[8 * i + 1]),
+                                           pack_bf16(f[8 * i + 2], f[8 * i + 3]),
+                                           pack_bf16(f[8 * i + 4], f[8 * i + 5]),
+                                           pack_bf16(f[8 * i + 6], f[8 * i + 7]));
+                    } else {
+                        for (int i = 0; i < 32 && col0 + i < pa.K; ++i)
+                            yp[i] = __float2bfloat16_rn(f[i]);
+                    }
+                }
+            }
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+        }
+    }
+
+    __syncwarp();
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == 1) ptx::tmem_dealloc(tmem_base, TCOLS);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+template <int BN>
+constexpr int b_stage_bytes() { return BN * 128; }
+
+int max_stages(int bn) {
+    int per = A_BYTES + bn * 128;
+    int s = (SMEM_LIMIT - SMEM_ALIGN - BAR_BYTES) / per;
+    return std::min(s, 12);
+}
+
+size_t smem_bytes(int bn, int stages) {
+    return (size_t)SMEM_ALIGN + (size_t)stages * (A_BYTES + bn * 128) + BAR_BYTES;
+}
+
+template <int BN, bool FP8, int G>
+gbconv_status_t launch_kernel(const FwdParams<G> &prm, int grid, cudaStream_t st) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(tc_fwd_kernel<BN, FP8, G>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    });
+    if (attr_err != cudaSuccess) return cuda_status(attr_err);
+    size_t smem = smem_bytes(BN, prm.stages);
+    tc_fwd_kernel<BN, FP8, G><<<grid, NTHREADS, smem, st>>>(prm);
+    return cuda_status(cudaGetLastError());
+}
+
+// Fills pa, tmA, tmB for one problem; bn is the tile width used.
+gbconv_status_t setup_problem(const Dims &d, int bn, const void *x, const void *w,
+                              const float *bias, const float *x_scale, const float *w_scale,
+                              void *y, ProbArgs &pa, CUtensorMap &ta, CUtensorMap &tb) {
+    const bool fp8 = d.in_dtype == GBCONV_E4M3;
+    const int eb = fp8 ? 1 : 2;
+    const int ke = 128 / eb;
+    gbconv_status_t s = encode_im2col_act(&ta, d, x, eb, ke, BM);
+    if (s != GBCONV_OK) return s;
+    uint64_t dims[3] = {(uint64_t)d.C, (uint64_t)d.R * d.S, (uint64_t)d.K};
+    uint64_t strides[2] = {(uint64_t)d.C * eb, (uint64_t)d.R * d.S * d.C * eb};
+    uint32_t box[3] = {(uint32_t)ke, 1, (uint32_t)bn};
+    s = encode_tiled(&tb, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                     w, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (s != GBCONV_OK) return s;
+    pa.M = (int)d.M();
+    pa.P = d.P;
+    pa.Q = d.Q;
+    pa.pw = d.pw;
+    pa.ph = d.ph;
+    pa.u = d.u;
+    pa.v = d.v;
+    pa.dh = d.dh;
+    pa.dw = d.dw;
+    pa.S = d.S;
+    pa.RS = d.R * d.S;
+    pa.c_blocks = (d.C + ke - 1) / ke;
+    pa.kb_per_tile = pa.RS * pa.c_blocks;
+    pa.n_tiles = (d.K + bn - 1) / bn;
+    pa.bn = bn;
+    pa.K = d.K;
+    pa.relu = (d.flags & GBCONV_FLAG_RELU) ? 1 : 0;
+    pa.out_f32 = d.out_dtype == GBCONV_F32;
+    pa.bias = (d.flags & GBCONV_FLAG_BIAS) ? bias : nullptr;
+    pa.x_scale = x_scale;
+    pa.w_scale = w_scale;
+    pa.y = y;
+    return GBCONV_OK;
+}
+
+int tiles_of(const ProbArgs &pa) { return ((pa.M + BM - 1) / BM) * pa.n_tiles; }
+
+}  // namespace
+
+bool tc_fwd_supported(const Dims &d) {
+    if (d.layout != GBCONV_NHWC) return false;
+    if (d.in_dtype == GBCONV_BF16) {
+        if (d.out_dtype != GBCONV_BF16 && d.out_dtype != GBCONV_F32) return false;
+        if (d.C % 8 || d.K % 8) return false;
+    } else if (d.in_dtype == GBCONV_E4M3) {
+        if (d.out_dtype != GBCONV_BF16) return false;
+        if (d.C % 16 || d.K % 8) return false;
+    } else {
+        return false;
+    }
+    // im2col bounding-box corners are signed 8-bit for 4-D maps
+    if (d.pw > 127 || d.ph > 127) return false;
+    if (d.pw - d.dw * (d.S - 1) < -128 || d.ph - d.dh * (d.R - 1) < -128) return false;
+    if (d.dw * (d.S - 1) > 65535 || d.dh * (d.R - 1) > 65535) return false;
+    if (d.u > 8 || d.v > 8) return false;  // TMA traversal stride limit
+    if (d.M() >= (1ll << 31)) return false;
+    return true;
+}
+
+TcConfig tc_fwd_default_config(const Dims &d) {
+    TcConfig c{};
+    if (d.K <= 32)
+        c.block_n = 32;
+    else if (d.K <= 64)
+        c.block_n = 64;
+    else if (d.K <= 128 || d.K % 256 != 0)
+        c.block_n = 128;
+    else
+        c.block_n = 256;
+    c.stages = max_stages(c.block_n);
+    c.split_k = 1;
+    c.raster = 0;
+    return c;
+}
+
+gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void *x,
+                              const void *w, const float *bias, const float *x_scale,
+                              const float *w_scale, void *y, cudaStream_t st) {
+    TcConfig cfg = cfg_in;
+    if (cfg.block_n != 32 && cfg.block_n != 64 && cfg.block_n != 128 && cfg.block_n != 256)
+        return GBCONV_ERR_INVALID_ARG;
+    if (cfg.stages < 2 || cfg.stages > max_stages(cfg.block_n)) cfg.stages = max_stages(cfg.block_n);
+    if (d.M() == 0) return GBCONV_OK;
+    FwdParams<1> prm;
+    memset(&prm, 0, sizeof(prm));
+    gbconv_status_t s = setup_problem(d, cfg.block_n, x, w, bias, x_scale, w_scale, y, prm.pa[0],
+                                      prm.tmA[0], prm.tmB[0]);
+    if (s != GBCONV_OK) return s;
+    prm.count = 1;
+    prm.tile_start[0] = 0;
+    prm.num_tiles = tiles_of(prm.pa[0]);
+    prm.tile_start[1] = prm.num_tiles;
+    prm.stages = cfg.stages;
+    prm.raster = cfg.raster;
+    prm.guard = make_guard();
+    if (!prm.guard.err) return GBCONV_ERR_CUDA;
+    int grid = std::min(prm.num_tiles, sm_count());
+    const bool fp8 = d.in_dtype == GBCONV_E4M3;
+    switch (cfg.block_n) {
+        case 32: return fp8 ? launch_kernel<32, true, 1>(prm, grid, st) : launch_kernel<32, false, 1>(prm, grid, st);
+        case 64: return fp8 ? launch_kernel<64, true, 1>(prm, grid, st) : launch_kernel<64, false, 1>(prm, grid, st);
+        case 128: return fp8 ? launch_kernel<128, true, 1>(prm, grid, st) : launch_kernel<128, false, 1>(prm, grid, st);
+        default: return fp8 ? launch_kernel<256, true, 1>(prm, grid, st) : launch_kernel<256, false, 1>(prm, grid, st);
+    }
+}
+
+// Grouped: problems are ordered by descending per-tile work (filter taps x
+// channel blocks x tile width) so that the static round-robin tile walk hands
+// every CTA a similar mix of long and short tiles.
+gbconv_status_t launch_tc_grouped(int count, const Dims *d, const TcConfig *cfg,
+                                  const void *const *x, const void *const *w,
+                                  const float *const *bias, void *const *y, cudaStream_t st) {
+    for (int base = 0; base < count; base += GMAX) {
+        const int cnt = std::min(GMAX, count - base);
+        std::vector<int> order(cnt);
+        for (int i = 0; i < cnt; ++i) order[i] = base + i;
+        auto work = [&](int i) {
+            const int ke = 64;
+            long long kb = (long long)d[i].R * d[i].S * ((d[i].C + ke - 1) / ke);
+            return kb * cfg[i].block_n;
+        };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+        static FwdParams<GMAX> prm;  // large: keep off the stack
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lock(mu);
+        memset(&prm, 0, sizeof(prm));
+        int tiles = 0, slot = 0;
+        for (int oi = 0; oi < cnt; ++oi) {
+            const int i = order[oi];
+            if (d[i].M() == 0) continue;
+            if (cfg[i].block_n != 32 && cfg[i].block_n != 64 && cfg[i].block_n != 128 &&
+                cfg[i].block_n != 256)
+                return GBCONV_ERR_INVALID_ARG;
+            gbconv_status_t s = setup_problem(d[i], cfg[i].block_n, x[i], w[i], bias[i], nullptr,
+                                              nullptr, y[i], prm.pa[slot], prm.tmA[slot],
+                                              prm.tmB[slot]);
+            if (s != GBCONV_OK) return s;
+            prm.tile_start[slot] = tiles;
+            tiles += tiles_of(prm.pa[slot]);
+            ++slot;
+        }
+        if (slot == 0) continue;
+        prm.tile_start[slot] = tiles;
+        prm.count = slot;
+        prm.num_tiles = tiles;
+        prm.stages = max_stages(256);
+        prm.raster = 0;
+        prm.guard = make_guard();
+        if (!prm.guard.err) return GBCONV_ERR_CUDA;
+        int grid = std::min(tiles, sm_count());
+        gbconv_status_t s = launch_kernel<256, false, GMAX>(prm, grid, st);
+        if (s != GBCONV_OK) return s;
+    }
+    return GBCONV_OK;
+}
+
+}  // namespace gbc

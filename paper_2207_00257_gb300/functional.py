@@ -1,0 +1,169 @@
+"""Torch-facing helpers over the C ABI: shape bookkeeping, output allocation
+through torch (PyTorch supplies device memory and streams only), status checks,
+and the autograd Function. Every arithmetic step runs in libgbconv's kernels.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+_DT = {torch.float32: B.GBCONV_F32, torch.bfloat16: B.GBCONV_BF16,
+       torch.float8_e4m3fn: B.GBCONV_E4M3, torch.uint8: B.GBCONV_E4M3}
+_TORCH = {B.GBCONV_F32: torch.float32, B.GBCONV_BF16: torch.bfloat16}
+
+
+def _pair(v):
+    return (v, v) if isinstance(v, int) else tuple(v)
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check_dev(*ts):
+    for t in ts:
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("gbconv expects contiguous CUDA tensors")
+
+
+def make_problem(x, w, stride=1, padding=0, dilation=1, layout="NHWC", out_dtype=None,
+                 bias=False, relu=False):
+    lay = B.GBCONV_NHWC if layout == "NHWC" else B.GBCONV_NCHW
+    if layout == "NHWC":
+        N, H, W, C = x.shape
+        K, R, S, C2 = w.shape
+    else:
+        N, C, H, W = x.shape
+        K, C2, R, S = w.shape
+    if C != C2:
+        raise ValueError(f"channel mismatch: x has {C}, w has {C2}")
+    ind = _DT[x.dtype]
+    outd = _DT[out_dtype] if out_dtype is not None else (B.GBCONV_BF16 if ind == B.GBCONV_E4M3 else ind)
+    flags = (B.GBCONV_FLAG_BIAS if bias else 0) | (B.GBCONV_FLAG_RELU if relu else 0)
+    return B.problem(N, C, H, W, K, R, S, _pair(stride), _pair(padding), _pair(dilation), ind,
+                     outd, lay, flags)
+
+
+def out_shape(prob, layout):
+    s, P, Q = B.gbconv_output_dims(prob)
+    B.check(s, "gbconv_output_dims")
+    return (prob.N, P, Q, prob.K) if layout == "NHWC" else (prob.N, prob.K, P, Q)
+
+
+def conv2d(x, w, bias=None, stride=1, padding=0, dilation=1, relu=False, layout="NHWC",
+           out_dtype=None, x_scale=None, w_scale=None, out=None):
+    """Forward convolution through conv2d_fwd. For E4M3 inputs pass the fp32
+    scales (x_scale: 1 element, w_scale: K elements) from quantize_e4m3."""
+    _check_dev(x, w, bias, x_scale, w_scale)
+    prob = make_problem(x, w, stride, padding, dilation, layout, out_dtype, bias is not None, relu)
+    if out is None:
+        out = torch.empty(out_shape(prob, layout), dtype=_TORCH[prob.out_dtype], device=x.device)
+    s = B.conv2d_fwd(prob, x.data_ptr(), w.data_ptr(), bias.data_ptr() if bias is not None else 0,
+                     x_scale.data_ptr() if x_scale is not None else 0,
+                     w_scale.data_ptr() if w_scale is not None else 0, out.data_ptr(), 0, 0,
+                     _stream())
+    B.check(s, "conv2d_fwd")
+    return out
+
+
+def workspace(op, prob, device):
+    s, nbytes = B.gbconv_workspace_size(op, prob)
+    B.check(s, "gbconv_workspace_size")
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device), nbytes
+
+
+def conv2d_dgrad(dy, w, x_shape, stride=1, padding=0, dilation=1, layout="NHWC", out_dtype=None):
+    """dL/dx for upstream gradient dy."""
+    _check_dev(dy, w)
+    fake_x = torch.empty(x_shape, dtype=dy.dtype, device="meta")
+    prob = make_problem(fake_x, w, stride, padding, dilation, layout, out_dtype)
+    dx = torch.empty(x_shape, dtype=_TORCH[prob.out_dtype], device=dy.device)
+    ws, nbytes = workspace(B.GBCONV_OP_DGRAD, prob, dy.device)
+    s = B.conv2d_dgrad(prob, dy.data_ptr(), w.data_ptr(), dx.data_ptr(), ws.data_ptr(), nbytes,
+                       _stream())
+    B.check(s, "conv2d_dgrad")
+    return dx
+
+
+def conv2d_wgrad(x, dy, w_shape, stride=1, padding=0, dilation=1, layout="NHWC", with_bias=True):
+    """(dL/dw, dL/db) in fp32 for upstream gradient dy."""
+    _check_dev(x, dy)
+    fake_w = torch.empty(w_shape, dtype=x.dtype, device="meta")
+    prob = make_problem(x, fake_w, stride, padding, dilation, layout)
+    dw = torch.empty(w_shape, dtype=torch.float32, device=x.device)
+    db = torch.empty(prob.K, dtype=torch.float32, device=x.device) if with_bias else None
+    ws, nbytes = workspace(B.GBCONV_OP_WGRAD, prob, x.device)
+    s = B.conv2d_wgrad(prob, x.data_ptr(), dy.data_ptr(), dw.data_ptr(),
+                       db.data_ptr() if db is not None else 0, ws.data_ptr(), nbytes, _stream())
+    B.check(s, "conv2d_wgrad")
+    return dw, db
+
+
+def quantize_e4m3(t, rows=1):
+    """Per-group FP8 preparation: returns (codes as float8_e4m3fn, fp32 scales[rows])."""
+    _check_dev(t)
+    out = torch.empty(t.shape, dtype=torch.float8_e4m3fn, device=t.device)
+    scale = torch.empty(rows, dtype=torch.float32, device=t.device)
+    s = B.gbconv_quantize_e4m3(t.data_ptr(), _DT[t.dtype], rows, t.numel() // rows,
+                               out.data_ptr(), scale.data_ptr(), _stream())
+    B.check(s, "gbconv_quantize_e4m3")
+    return out, scale
+
+
+def conv2d_grouped(xs, ws, biases, strides, pads, relu=False, outs=None):
+    """Many independent BF16 NHWC forward convolutions in one persistent launch."""
+    probs, ys = [], []
+    for i, (x, w) in enumerate(zip(xs, ws)):
+        _check_dev(x, w)
+        b = biases[i] if biases is not None else None
+        p = make_problem(x, w, strides[i], pads[i], 1, "NHWC", None, b is not None, relu)
+        probs.append(p)
+        ys.append(outs[i] if outs is not None else
+                  torch.empty(out_shape(p, "NHWC"), dtype=torch.bfloat16, device=x.device))
+    bias_ptrs = [b.data_ptr() if b is not None else 0 for b in (biases or [None] * len(xs))]
+    s = B.conv2d_grouped(len(probs), probs, [x.data_ptr() for x in xs], [w.data_ptr() for w in ws],
+                         bias_ptrs if biases is not None else None, [y.data_ptr() for y in ys],
+                         0, 0, _stream())
+    B.check(s, "conv2d_grouped")
+    return ys
+
+
+def device_error():
+    """Synchronise the current stream; raise if a bounded in-kernel wait ran out."""
+    B.check(B.gbconv_get_device_error(_stream()), "device")
+
+
+class Conv2dFn(torch.autograd.Function):
+    """y = conv2d(x, w) + b (optionally ReLU) with hand-written backward
+    kernels: conv2d_dgrad for dx and conv2d_wgrad for dw, db."""
+
+    @staticmethod
+    def forward(ctx, x, w, b, stride, padding, dilation, relu, layout):
+        y = conv2d(x, w, b, stride, padding, dilation, relu, layout)
+        ctx.save_for_backward(x, w, y if relu else None)
+        ctx.conf = (stride, padding, dilation, relu, layout, b is not None, b.dtype if b is not None else None)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, w, y = ctx.saved_tensors
+        stride, padding, dilation, relu, layout, has_b, bdt = ctx.conf
+        gy = gy.contiguous()
+        if relu:
+            gy = gy * (y > 0).to(gy.dtype)  # derivative of max(., 0); mask only
+        gy = gy.to(x.dtype).contiguous()
+        dx = dw = db = None
+        if ctx.needs_input_grad[0]:
+            dx = conv2d_dgrad(gy, w, tuple(x.shape), stride, padding, dilation, layout,
+                              out_dtype=x.dtype)
+        if ctx.needs_input_grad[1] or (has_b and ctx.needs_input_grad[2]):
+            dw32, db32 = conv2d_wgrad(x, gy, tuple(w.shape), stride, padding, dilation, layout,
+                                      with_bias=has_b)
+            dw = dw32.to(w.dtype)
+            db = db32.to(bdt) if has_b else None
+        return dx, dw, db, None, None, None, None, None
+
+
+def conv2d_autograd(x, w, b=None, stride=1, padding=0, dilation=1, relu=False, layout="NHWC"):
+    return Conv2dFn.apply(x, w, b, stride, padding, dilation, relu, layout)

@@ -1,0 +1,92 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI
+and the FP64 oracle on the same seeded inputs, and measure the normalised
+error  max |got - ref| / (|b| + sum |x||w|)."""
+import numpy as np
+import torch
+
+import oracle
+from paper_2207_00257_gb300 import binding as B
+from paper_2207_00257_gb300 import functional as F
+from paper_2207_00257_gb300.synth import ConvShape, make_inputs, sample_indices
+
+# tolerances (normalised error); see the design doc for their derivation
+TOL_F32 = 1e-5          # FP32 FFMA path vs FP64
+TOL_BF16_OUT = 4e-3     # BF16-rounded output vs oracle on the same (rounded) inputs
+TOL_BF16 = 1e-2         # BF16 path vs oracle on the FP32 master values
+TOL_FP8 = 5e-2          # FP8 path vs oracle on the FP32 master values
+TOL_ACC32 = 1e-5        # FP32 output of a BF16/FP8 product sum vs oracle on rounded inputs
+
+
+def oconv(sh: ConvShape) -> oracle.Conv:
+    return oracle.Conv(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                       sh.layout)
+
+
+def f64(t):
+    return t.detach().double().cpu().numpy()
+
+
+def set_block_n(sh, in_dtype, out_dtype, block_n, flags=0, raster=0):
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                     in_dtype, out_dtype, B.GBCONV_NHWC if sh.layout == "NHWC" else B.GBCONV_NCHW,
+                     flags)
+    B.check(B.gbconv_set_config(B.GBCONV_OP_FWD, prob, B.gbconv_config_t(block_n, 0, 0, raster)),
+            "set_config")
+
+
+def fwd_case(sh: ConvShape, dtype=torch.bfloat16, out_dtype=None, relu=True, bias=True, seed=0,
+             x_dist="normal", w_dist="he", idx=None):
+    """Runs the GPU forward; returns dict(err_i, err_ii, y) where err_i is vs the
+    oracle on the inputs as the GPU saw them, err_ii vs the FP32 master values."""
+    x, w, b, _ = make_inputs(sh, seed, x_dist, w_dist, bias)
+    dev = torch.device("cuda")
+    if dtype == torch.float32:
+        xg, wg = x, w
+    else:
+        xg, wg = x.to(dtype), w.to(dtype)
+    y = F.conv2d(xg.to(dev), wg.to(dev), b.to(dev) if b is not None else None, sh.stride,
+                 sh.pad, sh.dil, relu, sh.layout, out_dtype)
+    F.device_error()
+    p = oconv(sh)
+    bd = f64(b) if b is not None else None
+    got = f64(y).reshape(-1)
+    if idx is not None:
+        got = got[idx]
+    ref, bound = oracle.conv2d_fwd(p, f64(xg), f64(wg), bd, relu, idx=idx, with_bound=True)
+    ref2, bound2 = oracle.conv2d_fwd(p, f64(x), f64(w), bd, relu, idx=idx, with_bound=True)
+    return dict(err_i=oracle.max_normalised_error(got, ref.reshape(-1), bound.reshape(-1)),
+                err_ii=oracle.max_normalised_error(got, ref2.reshape(-1), bound2.reshape(-1)),
+                y=y, ref=ref, got=got)
+
+
+def fp8_case(sh: ConvShape, seed=0, relu=False, bias=True, idx=None):
+    """FP8 path: GPU quantises x (per tensor) and w (per output channel), runs
+    the E4M3 convolution; compared with the oracle on (a) the dequantised
+    operands and (b) the FP32 master values."""
+    x, w, b, _ = make_inputs(sh, seed, "relu_normal", "he", bias)
+    dev = torch.device("cuda")
+    xq, xs = F.quantize_e4m3(x.to(dev), rows=1)
+    wq, ws = F.quantize_e4m3(w.to(dev), rows=sh.K)
+    y = F.conv2d(xq, wq, b.to(dev) if b is not None else None, sh.stride, sh.pad, sh.dil, relu,
+                 "NHWC", torch.bfloat16, x_scale=xs, w_scale=ws)
+    F.device_error()
+    p = oconv(sh)
+    codes_x = xq.view(torch.uint8).cpu().numpy()
+    codes_w = wq.view(torch.uint8).cpu().numpy()
+    sx = xs.cpu().numpy().astype(np.float64)
+    sw = ws.cpu().numpy().astype(np.float64)
+    xd = oracle.e4m3_to_f64(codes_x) * sx[0]
+    wd = oracle.e4m3_to_f64(codes_w) * sw[:, None, None, None]
+    bd = f64(b) if b is not None else None
+    got = f64(y).reshape(-1)
+    if idx is not None:
+        got = got[idx]
+    ref, bound = oracle.conv2d_fwd(p, xd, wd, bd, relu, idx=idx, with_bound=True)
+    ref2, bound2 = oracle.conv2d_fwd(p, f64(x), f64(w), bd, relu, idx=idx, with_bound=True)
+    return dict(err_i=oracle.max_normalised_error(got, ref.reshape(-1), bound.reshape(-1)),
+                err_ii=oracle.max_normalised_error(got, ref2.reshape(-1), bound2.reshape(-1)),
+                xq=xq, xs=xs, wq=wq, ws=ws, x=x, w=w)
+
+
+def sampled(total, count=1500, seed=123):
+    return sample_indices(total, count, seed)

@@ -1,0 +1,39 @@
+"""Failure detection without a GPU fault: the test control
+GBCONV_DEBUG_SKIP_LOADS makes the tensor-core producer issue no loads, so the
+consumers' bounded waits run out; the kernel must record a timeout, free its
+Tensor Memory and return, and the context must stay usable."""
+import pytest
+import torch
+
+from paper_2207_00257_gb300 import binding as B
+from paper_2207_00257_gb300 import functional as F
+from paper_2207_00257_gb300.synth import ConvShape, make_inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def test_wait_timeout_reported_and_context_survives():
+    sh = ConvShape(2, 64, 9, 9, 64, 3, 3, 1, 1, 1)
+    x, w, b, _ = make_inputs(sh, 40)
+    xb, wb, bb = x.bfloat16().cuda(), w.bfloat16().cuda(), b.cuda()
+    ref = F.conv2d(xb, wb, bb, 1, 1, 1, True)
+    F.device_error()
+    B.check(B.gbconv_debug_set(B.GBCONV_DEBUG_WAIT_LIMIT_NS, 20_000_000), "debug")  # 20 ms
+    B.check(B.gbconv_debug_set(B.GBCONV_DEBUG_SKIP_LOADS, 1), "debug")
+    try:
+        F.conv2d(xb, wb, bb, 1, 1, 1, True)
+        st = B.gbconv_get_device_error(torch.cuda.current_stream().cuda_stream)
+        assert st == B.GBCONV_ERR_TIMEOUT
+    finally:
+        B.gbconv_debug_set(B.GBCONV_DEBUG_SKIP_LOADS, 0)
+        B.gbconv_debug_set(B.GBCONV_DEBUG_WAIT_LIMIT_NS, 0)
+    # the word was cleared and the next launch (which needs all TMEM) works
+    y = F.conv2d(xb, wb, bb, 1, 1, 1, True)
+    F.device_error()
+    assert torch.equal(y, ref)

@@ -1,0 +1,105 @@
+"""GPU parity of the grouped (many problems, one persistent launch) forward,
+including replay from a captured CUDA graph."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2207_00257_gb300 import binding as B
+from paper_2207_00257_gb300 import functional as F
+from paper_2207_00257_gb300.synth import ConvShape, grouped_problems, make_inputs
+
+from _gpu_helpers import TOL_BF16, TOL_BF16_OUT, f64, oconv, sampled
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _inputs(shapes, seed0):
+    xs, ws, bs, masters = [], [], [], []
+    for i, sh in enumerate(shapes):
+        x, w, b, _ = make_inputs(sh, seed0 + i)
+        xs.append(x.bfloat16().cuda())
+        ws.append(w.bfloat16().cuda())
+        bs.append(b.cuda())
+        masters.append((x, w, b))
+    return xs, ws, bs, masters
+
+
+def _check(shapes, xs, ws, bs, masters, ys, relu, max_points=None):
+    for i, sh in enumerate(shapes):
+        p = oconv(sh)
+        idx = None
+        total = int(np.prod(sh.y_shape()))
+        if max_points is not None and total > max_points:
+            idx = sampled(total, max_points, seed=500 + i)
+        got = f64(ys[i]).reshape(-1)
+        if idx is not None:
+            got = got[idx]
+        ref, bound = oracle.conv2d_fwd(p, f64(xs[i]), f64(ws[i]), f64(bs[i]), relu, idx=idx,
+                                       with_bound=True)
+        e = oracle.max_normalised_error(got, ref.reshape(-1), bound.reshape(-1))
+        assert e <= TOL_BF16_OUT, (i, sh, e)
+        x, w, b = masters[i]
+        ref2, bound2 = oracle.conv2d_fwd(p, f64(x), f64(w), f64(b), relu, idx=idx,
+                                         with_bound=True)
+        e2 = oracle.max_normalised_error(got, ref2.reshape(-1), bound2.reshape(-1))
+        assert e2 <= TOL_BF16, (i, sh, e2)
+
+
+SMALL = [
+    ConvShape(2, 64, 9, 9, 64, 3, 3, 1, 1, 1),
+    ConvShape(1, 16, 14, 14, 32, 1, 1, 1, 0, 1),
+    ConvShape(3, 128, 7, 7, 256, 3, 3, 1, 1, 1),
+    ConvShape(2, 32, 15, 15, 48, 5, 5, 2, 2, 1),
+    ConvShape(1, 48, 28, 28, 16, 7, 7, 2, 3, 1),
+    ConvShape(4, 256, 4, 4, 128, 1, 1, 1, 0, 1),
+]
+
+
+def test_grouped_small():
+    xs, ws, bs, masters = _inputs(SMALL, 600)
+    strides = [s.stride for s in SMALL]
+    pads = [s.pad for s in SMALL]
+    ys = F.conv2d_grouped(xs, ws, bs, strides, pads, relu=True)
+    F.device_error()
+    _check(SMALL, xs, ws, bs, masters, ys, relu=True)
+
+
+def test_grouped_matches_single_launches_bitwise():
+    xs, ws, bs, _ = _inputs(SMALL, 610)
+    ys = F.conv2d_grouped(xs, ws, bs, [s.stride for s in SMALL], [s.pad for s in SMALL])
+    for i, sh in enumerate(SMALL):
+        y1 = F.conv2d(xs[i], ws[i], bs[i], sh.stride, sh.pad, 1, False, "NHWC")
+        F.device_error()
+        assert torch.equal(y1, ys[i]), i
+
+
+def test_grouped_workload_64_problems_graph():
+    """The 64-problem workload (shapes drawn from seed 1, committed JSON), one
+    persistent launch captured in a CUDA graph and replayed; sampled outputs
+    of every problem against the oracle."""
+    shapes = grouped_problems()
+    assert len(shapes) == 64
+    xs, ws, bs, masters = _inputs(shapes, 1000)
+    ys = [torch.empty(s.y_shape(), dtype=torch.bfloat16, device="cuda") for s in shapes]
+    strides = [s.stride for s in shapes]
+    pads = [s.pad for s in shapes]
+    F.conv2d_grouped(xs, ws, bs, strides, pads, relu=True, outs=ys)  # warm-up (sets attributes)
+    torch.cuda.synchronize()
+    for y in ys:
+        y.fill_(0)
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            F.conv2d_grouped(xs, ws, bs, strides, pads, relu=True, outs=ys)
+    graph.replay()
+    torch.cuda.synchronize()
+    F.device_error()
+    _check(shapes, xs, ws, bs, masters, ys, relu=True, max_points=300)
