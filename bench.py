@@ -155,8 +155,11 @@ def capture_steps(launch_fns, steps, nsets, torch, timed_events=True):
     callables f(set_index, stream). Returns (graph, events[steps][len][2])."""
     stream = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
-    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            for _ in launch_fns] for _ in range(steps)] if timed_events else None
+    def ev():
+        # "external" events become record nodes of the graph, so they can be timed
+        return torch.cuda.Event(enable_timing=True, external=True)
+
+    evs = [[(ev(), ev()) for _ in launch_fns] for _ in range(steps)] if timed_events else None
     with torch.cuda.stream(stream):
         with torch.cuda.graph(g, stream=stream):
             for st in range(steps):

@@ -70,7 +70,9 @@ typedef enum { GBCONV_OP_FWD = 0, GBCONV_OP_DGRAD = 1, GBCONV_OP_WGRAD = 2 } gbc
  *   BF16 -> BF16 or F32   NHWC, C % 8 == 0, K % 8 == 0 (tensor cores, FP32 accumulate)
  *   E4M3 -> BF16  NHWC, C % 16 == 0, K % 8 == 0 (tensor cores, FP32 accumulate,
  *                 y = b + x_scale * w_scale[k] * sum(xq * wq))
- * Padding must be in [0, 127] and dilation*(R-1) <= 127 (the im2col TMA range). */
+ * Padding must be in [0, 127] and dilation*(R-1) <= 127 (the im2col TMA range).
+ * N may be 0 (an empty batch): conv2d_fwd and conv2d_dgrad then do nothing
+ * (tensor pointers may be NULL) and conv2d_wgrad writes zeros to dw and db. */
 typedef struct {
     int32_t N, C, H, W, K, R, S;
     int32_t stride_h, stride_w;

@@ -313,6 +313,7 @@ gbconv_status_t conv2d_fwd(const gbconv_problem_t *prob, const void *x, const vo
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
+    if (d.N == 0) return GBCONV_OK;  // empty batch: nothing to read or write
     if (!x || !w || !y || ((d.flags & GBCONV_FLAG_BIAS) && !bias)) return GBCONV_ERR_INVALID_ARG;
     if (x == y || w == y) return GBCONV_ERR_INVALID_ARG;
     return do_fwd(d, config_for(GBCONV_OP_FWD, *prob, d), x, w, bias, x_scale, w_scale, y,
@@ -324,6 +325,7 @@ gbconv_status_t conv2d_dgrad(const gbconv_problem_t *prob, const void *dy, const
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
+    if (d.N == 0) return GBCONV_OK;  // empty batch: dx is empty
     if (!dy || !w || !dx || dx == dy || dx == w) return GBCONV_ERR_INVALID_ARG;
     return do_dgrad(d, config_for(GBCONV_OP_DGRAD, *prob, d), dy, w, dx, ws, ws_bytes,
                     static_cast<cudaStream_t>(stream));
@@ -335,7 +337,7 @@ gbconv_status_t conv2d_wgrad(const gbconv_problem_t *prob, const void *x, const 
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
-    if (!x || !dy || !dw) return GBCONV_ERR_INVALID_ARG;
+    if (!dw || (d.N > 0 && (!x || !dy))) return GBCONV_ERR_INVALID_ARG;
     return do_wgrad(d, config_for(GBCONV_OP_WGRAD, *prob, d), x, dy, dw, db, ws, ws_bytes,
                     static_cast<cudaStream_t>(stream));
 }
