@@ -201,6 +201,31 @@ const char *gbconv_status_string(gbconv_status_t status);
 #define GBCONV_DEBUG_SKIP_LOADS 2
 gbconv_status_t gbconv_debug_set(int32_t key, int64_t value);
 
+/* Data gradient that allocates nothing, for callers that cannot call
+ * cudaMalloc or hand the library a workspace: code running under a framework
+ * whose own allocator must own every device byte, code with a device-memory
+ * budget fixed at start-up, and code that enqueues work where an allocation
+ * would stall or be refused. The paper has no counterpart: it is a packaging
+ * variant of conv2d_dgrad, not part of the method.
+ *
+ * Same arguments, layouts and results as conv2d_dgrad minus the workspace.
+ * Where conv2d_dgrad would place the rotated filter in the caller's workspace
+ * (BF16 NHWC, stride 1), this entry point uses a static device array of
+ * GBCONV_DGRAD_STATIC_SCRATCH_BYTES bytes that the library holds on every GPU
+ * that loads it, until the process exits. Filters whose K*R*S*C*2 bytes exceed
+ * that size are refused with GBCONV_ERR_WORKSPACE before anything is enqueued.
+ * Problems conv2d_dgrad runs on the CUDA-core kernel need no scratch at all.
+ *
+ * The first call on each device looks up the array's device address (a CUDA
+ * runtime query, done once per device with that device current); make that
+ * first call before capturing a stream. Every call on a device shares the one
+ * array and overwrites all of the scratch it reads, so no clearing is needed,
+ * but calls that overlap on the same GPU (other streams, other host threads)
+ * race on it: serialise them. */
+#define GBCONV_DGRAD_STATIC_SCRATCH_BYTES (8u * 1024u * 1024u)
+gbconv_status_t conv2d_dgrad_noalloc(const gbconv_problem_t *prob, const void *dy,
+                                     const void *w, void *dx, gbconv_stream_t stream);
+
 /* Library version, as major*10000 + minor*100 + patch. */
 int32_t gbconv_version(void);
 

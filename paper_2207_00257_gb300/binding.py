@@ -33,7 +33,7 @@ EXPORTS = [
     "conv2d_wgrad", "conv2d_grouped", "gbconv_quantize_e4m3", "gbconv_get_config",
     "gbconv_set_config", "gbconv_tune", "gbconv_tune_cache_save", "gbconv_tune_cache_load",
     "gbconv_get_device_error", "gbconv_status_string", "gbconv_debug_set", "gbconv_version",
-    "gbconv_shutdown",
+    "gbconv_shutdown", "conv2d_dgrad_noalloc",
 ]
 
 
@@ -85,6 +85,7 @@ _SIGS = {
     "gbconv_debug_set": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64]),
     "gbconv_version": (ctypes.c_int32, []),
     "gbconv_shutdown": (None, []),
+    "conv2d_dgrad_noalloc": (ctypes.c_int, [_PROB, _P, _P, _P, _P]),
 }
 
 
@@ -221,3 +222,10 @@ def gbconv_version():
 
 def gbconv_shutdown():
     lib().gbconv_shutdown()
+
+
+GBCONV_DGRAD_STATIC_SCRATCH_BYTES = 8 * 1024 * 1024
+
+
+def conv2d_dgrad_noalloc(prob, dy, w, dx, stream):
+    return lib().conv2d_dgrad_noalloc(ctypes.byref(prob), _vp(dy), _vp(w), _vp(dx), _vp(stream))

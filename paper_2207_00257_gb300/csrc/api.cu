@@ -17,6 +17,10 @@
 // memory: nothing is allocated for it).
 __device__ unsigned int g_gbconv_error_word;
 
+// Scratch of conv2d_dgrad_noalloc: the rotated filter lives here instead of in
+// a caller's workspace. Every GPU that loads the library holds it until exit.
+static __device__ __align__(256) unsigned char g_dgrad_static_scratch[GBCONV_DGRAD_STATIC_SCRATCH_BYTES];
+
 namespace gbc {
 namespace {
 
@@ -581,6 +585,49 @@ gbconv_status_t gbconv_debug_set(int32_t key, int64_t value) {
         return GBCONV_OK;
     }
     return GBCONV_ERR_INVALID_ARG;
+}
+
+// Device address of g_dgrad_static_scratch on the current device. In host
+// code the array's name is only a host-side stand-in, so the real address is
+// looked up once per device (with that device current) and cached.
+static gbconv_status_t dgrad_static_scratch(void **out) {
+    static std::mutex mu;
+    static void *addr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GBCONV_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_dgrad_static_scratch) != cudaSuccess || !p)
+            return GBCONV_ERR_CUDA;
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return GBCONV_OK;
+}
+
+gbconv_status_t conv2d_dgrad_noalloc(const gbconv_problem_t *prob, const void *dy, const void *w,
+                                     void *dx, gbconv_stream_t stream) {
+    Dims d;
+    gbconv_status_t s = make_dims(prob, &d);
+    if (s != GBCONV_OK) return s;
+    if (d.N == 0) return GBCONV_OK;
+    if (!dy || !w || !dx || dx == dy || dx == w) return GBCONV_ERR_INVALID_ARG;
+    if (d.in_dtype == GBCONV_E4M3 || d.out_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
+    if (d.in_dtype == GBCONV_F32 && d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Dims t;
+    if (!dgrad_as_fwd(d, &t)) return launch_simt_dgrad(d, dy, w, dx, st);  // no scratch used
+    const size_t need = (size_t)d.K * d.R * d.S * d.C * 2;
+    if (need > (size_t)GBCONV_DGRAD_STATIC_SCRATCH_BYTES) return GBCONV_ERR_WORKSPACE;
+    if (!aligned16(dy) || !aligned16(dx)) return GBCONV_ERR_ALIGNMENT;
+    void *scratch = nullptr;
+    s = dgrad_static_scratch(&scratch);
+    if (s != GBCONV_OK) return s;
+    s = launch_rotate_filter(d, w, scratch, st);
+    if (s != GBCONV_OK) return s;
+    return launch_tc_fwd(t, config_for(GBCONV_OP_DGRAD, *prob, d), dy, scratch, nullptr, nullptr,
+                         nullptr, dx, st);
 }
 
 int32_t gbconv_version(void) { return 10000; }
