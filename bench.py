@@ -248,6 +248,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline BF16 layer set (skip FP32/FP8/grouped/backward)")
+    ap.add_argument("--sections", default="fp32,fp8,grouped,backward",
+                    help="comma list of extra workloads to run after the headline layer set")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -317,10 +319,11 @@ def run_ours(args, rank, world, local):
     out["e2e"] = e2e_resnet(layers, torch, dist_on, world, max(3, min(args.steps, 20)))
     # ---- extras: FP32 kernel, FP8, grouped, backward ----
     if not args.no_extras:
-        out["fp32"] = bench_fp32(torch, dev, args, dist_on, pk)
-        out["fp8"] = bench_fp8(torch, dev, args, dist_on, pk)
-        out["grouped"] = bench_grouped(torch, dev, args, dist_on, pk)
-        out["backward"] = bench_backward(torch, dev, args, dist_on, pk)
+        sections = [x for x in args.sections.split(",") if x]
+        fns = {"fp32": bench_fp32, "fp8": bench_fp8, "grouped": bench_grouped,
+               "backward": bench_backward}
+        for name in sections:
+            out[name] = fns[name](torch, dev, args, dist_on, pk)
     sampler.stop()
     out["clocks"] = sampler.summary(*clocks_window)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -552,7 +555,7 @@ def oracle_sample_run(images, nthreads=0):
 def cpu_baseline(layers, torch):
     import numpy as np
     import oracle
-    images = int(os.environ.get("GBCONV_CPU_SAMPLE_IMAGES", "4"))
+    images = int(os.environ.get("GBCONV_CPU_SAMPLE_IMAGES", "32"))
     secs, flops, outs = oracle_sample_run(images)
     errs = {}
     # refresh the outputs of buffer set 0 (the oracle's inputs) and compare

@@ -188,9 +188,13 @@ TcConfig config_for(int op, const gbconv_problem_t &p, const Dims &d) {
     return c;
 }
 
+// Bias-gradient partial sums: a fixed number of row slices, independent of
+// the weight gradient's split.
+constexpr int BIAS_SLICES = 128;
+
 size_t wgrad_ws_bytes(const Dims &d, int slices) {
     size_t kcrs = (size_t)d.K * d.C * d.R * d.S;
-    return round256((size_t)slices * (kcrs + (size_t)d.K) * sizeof(float));
+    return round256(((size_t)slices * kcrs + (size_t)BIAS_SLICES * d.K) * sizeof(float));
 }
 
 gbconv_status_t do_fwd(const Dims &d, const TcConfig &cfg, const void *x, const void *w,
@@ -229,8 +233,11 @@ gbconv_status_t do_wgrad(const Dims &d, const TcConfig &cfg, const void *x, cons
                          float *dw, float *db, void *ws, size_t ws_bytes, cudaStream_t st) {
     if (d.in_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
     const long long kcrs = (long long)d.K * d.C * d.R * d.S;
-    const int slices = std::max(1, cfg.split_k);
+    const bool tc = tc_wgrad_supported(d) && aligned16(x) && aligned16(dy) && aligned16(ws);
+    int slices = std::max(1, cfg.split_k);
     if (slices > 1024) return GBCONV_ERR_INVALID_ARG;
+    // the tensor-core kernel gives every slice at least one 64-pixel step
+    if (tc) slices = (int)std::max<long long>(1, std::min<long long>(slices, tc_wgrad_pixel_steps(d)));
     size_t need = wgrad_ws_bytes(d, slices);
     if (!ws || ws_bytes < need) return GBCONV_ERR_WORKSPACE;
     float *part = static_cast<float *>(ws);
@@ -241,17 +248,16 @@ gbconv_status_t do_wgrad(const Dims &d, const TcConfig &cfg, const void *x, cons
         return cuda_status(e);
     }
     gbconv_status_t s;
-    if (tc_wgrad_supported(d) && aligned16(x) && aligned16(dy))
-        s = launch_tc_wgrad_partials(d, cfg, x, dy, part, st);
-    else
+    if (tc) {
+        TcConfig c = cfg;
+        c.split_k = slices;
+        s = launch_tc_wgrad_partials(d, c, x, dy, part, st);
+    } else
         s = launch_simt_wgrad_partials(d, x, dy, part, slices, st);
     if (s != GBCONV_OK) return s;
     s = launch_reduce_slices(part, slices, kcrs, dw, st);
     if (s != GBCONV_OK) return s;
-    if (db) {
-        int bs = std::min(slices, 64);
-        s = launch_bias_grad(d, dy, db, bpart, bs, st);
-    }
+    if (db) s = launch_bias_grad(d, dy, db, bpart, BIAS_SLICES, st);
     return s;
 }
 

@@ -41,15 +41,36 @@ __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// NHWC: g is [M][K]; block y = slice of rows, threads stride over k.
+// NHWC: g is [M][K]. Block (x, y) sums the 32 channels k = 32x + lane over
+// the rows of slice y; its 8 warps take interleaved rows (row = r0 + warp +
+// 8i), each with a compensated running sum, then a fixed-shape tree joins the
+// 8 warp sums. Loads are 64-byte coalesced runs along k.
 template <typename T>
-__global__ void bias_grad_nhwc(const T *__restrict__ g, long long M, int K, int slices,
-                               float *__restrict__ part) {
-    long long r0 = M * blockIdx.y / slices, r1 = M * (blockIdx.y + 1) / slices;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
-        float sum = 0.f, comp = 0.f;
-        for (long long r = r0; r < r1; ++r) neumaier(sum, comp, to_f(g[r * K + k]));
-        part[(long long)blockIdx.y * K + k] = sum + comp;
+__global__ void __launch_bounds__(256) bias_grad_nhwc(const T *__restrict__ g, long long M, int K,
+                                                      int slices, float *__restrict__ part) {
+    __shared__ float sh[8][33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + lane;
+    const long long r0 = M * blockIdx.y / slices, r1 = M * (blockIdx.y + 1) / slices;
+    float sum = 0.f, comp = 0.f;
+    if (k < K) {
+        long long r = r0 + wid;
+        for (; r + 24 < r1; r += 32) {  // four independent loads in flight
+            const float a = to_f(g[r * K + k]), b = to_f(g[(r + 8) * K + k]);
+            const float c = to_f(g[(r + 16) * K + k]), e = to_f(g[(r + 24) * K + k]);
+            neumaier(sum, comp, a);
+            neumaier(sum, comp, b);
+            neumaier(sum, comp, c);
+            neumaier(sum, comp, e);
+        }
+        for (; r < r1; r += 8) neumaier(sum, comp, to_f(g[r * K + k]));
+    }
+    sh[wid][lane] = sum + comp;
+    __syncthreads();
+    if (wid == 0 && k < K) {
+        float a = (sh[0][lane] + sh[1][lane]) + (sh[2][lane] + sh[3][lane]);
+        float b = (sh[4][lane] + sh[5][lane]) + (sh[6][lane] + sh[7][lane]);
+        part[(long long)blockIdx.y * K + k] = a + b;
     }
 }
 
@@ -93,15 +114,44 @@ __global__ void rotate_krsc(const T *__restrict__ w, T *__restrict__ wr, int K, 
     }
 }
 
-// amax per group into amax_bits[r] (non-negative floats order like their bits).
-template <typename T>
+// Vector of 8 consecutive input values as float (16 B of BF16, or two 16-B
+// loads of FP32). The caller guarantees alignment and bounds.
+__device__ __forceinline__ void load8(const float *p, float (&v)[8]) {
+    float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void load8(const __nv_bfloat16 *p, float (&v)[8]) {
+    uint4 u = *reinterpret_cast<const uint4 *>(p);
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float2 f = __bfloat1622float2(h[i]);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+
+// amax per group into amax_bits[r] (non-negative floats order like their
+// bits). VEC: 8 values per thread step (requires len % 8 == 0 and 16-byte
+// aligned groups), else one value per step.
+template <typename T, bool VEC>
 __global__ void amax_kernel(const T *__restrict__ in, long long len, unsigned *__restrict__ amax_bits) {
     __shared__ float sh[256];
-    const long long base = (long long)blockIdx.y * len;
+    const T *g = in + (long long)blockIdx.y * len;
     float m = 0.f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
-         i += (long long)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(to_f(in[base + i])));
+    if (VEC) {
+        for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 8; i < len;
+             i += (long long)gridDim.x * blockDim.x * 8) {
+            float v[8];
+            load8(g + i, v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) m = fmaxf(m, fabsf(v[k]));
+        }
+    } else {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+             i += (long long)gridDim.x * blockDim.x)
+            m = fmaxf(m, fabsf(to_f(g[i])));
+    }
     sh[threadIdx.x] = m;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -116,15 +166,32 @@ __device__ __forceinline__ float scale_of(unsigned amax_bits) {
     return (s >= 1.0e-12f) ? s : 1.0e-12f;
 }
 
-template <typename T>
+__device__ __forceinline__ uint8_t e4m3_of(float v, float s) {
+    return (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(v, s), __NV_SATFINITE, __NV_E4M3);
+}
+
+template <typename T, bool VEC>
 __global__ void quant_kernel(const T *__restrict__ in, long long len,
                              const unsigned *__restrict__ amax_bits, uint8_t *__restrict__ out) {
     const long long base = (long long)blockIdx.y * len;
     const float s = scale_of(amax_bits[blockIdx.y]);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
-         i += (long long)gridDim.x * blockDim.x) {
-        float q = __fdiv_rn(to_f(in[base + i]), s);
-        out[base + i] = (uint8_t)__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+    if (VEC) {
+        for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 8; i < len;
+             i += (long long)gridDim.x * blockDim.x * 8) {
+            float v[8];
+            load8(in + base + i, v);
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                lo |= (uint32_t)e4m3_of(v[k], s) << (8 * k);
+                hi |= (uint32_t)e4m3_of(v[4 + k], s) << (8 * k);
+            }
+            *reinterpret_cast<uint2 *>(out + base + i) = make_uint2(lo, hi);
+        }
+    } else {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
+             i += (long long)gridDim.x * blockDim.x)
+            out[base + i] = e4m3_of(to_f(in[base + i]), s);
     }
 }
 
@@ -156,7 +223,7 @@ gbconv_status_t launch_reduce_slices(const float *ws, int slices, long long n, f
 gbconv_status_t launch_bias_grad(const Dims &d, const void *g, float *db, float *ws, int slices,
                                  cudaStream_t st) {
     if (d.layout == GBCONV_NHWC) {
-        dim3 grid((unsigned)((d.K + 255) / 256), (unsigned)slices);
+        dim3 grid((unsigned)((d.K + 31) / 32), (unsigned)slices);
         if (d.in_dtype == GBCONV_F32)
             bias_grad_nhwc<float><<<grid, 256, 0, st>>>((const float *)g, d.M(), d.K, slices, ws);
         else
@@ -195,21 +262,28 @@ gbconv_status_t launch_quantize_e4m3(const void *in, int in_dtype, long long row
     unsigned *amax = reinterpret_cast<unsigned *>(scale);
     cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float) * rows, st);
     if (e != cudaSuccess) return cuda_status(e);
-    long long per = (len + 255) / 256;
+    const int eb = in_dtype == GBCONV_F32 ? 4 : 2;
+    const bool vec = len % 8 == 0 && (reinterpret_cast<uintptr_t>(in) % 16) == 0 &&
+                     (reinterpret_cast<uintptr_t>(out) % 8) == 0 && (len * eb) % 16 == 0;
+    const long long per = vec ? (len / 8 + 255) / 256 : (len + 255) / 256;
     unsigned gx = (unsigned)(per < 1 ? 1 : per);
     unsigned cap = (unsigned)((sm_count() * 8 + rows - 1) / rows);
     if (cap < 1) cap = 1;
     if (gx > cap) gx = cap;
     dim3 grid(gx, (unsigned)rows);
+#define GBC_QUANT(T, V)                                                                  \
+    do {                                                                               \
+        amax_kernel<T, V><<<grid, 256, 0, st>>>((const T *)in, len, amax);             \
+        quant_kernel<T, V><<<grid, 256, 0, st>>>((const T *)in, len, amax, out);       \
+    } while (0)
     if (in_dtype == GBCONV_F32) {
-        amax_kernel<float><<<grid, 256, 0, st>>>((const float *)in, len, amax);
-        quant_kernel<float><<<grid, 256, 0, st>>>((const float *)in, len, amax, out);
+        if (vec) GBC_QUANT(float, true); else GBC_QUANT(float, false);
     } else if (in_dtype == GBCONV_BF16) {
-        amax_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16 *)in, len, amax);
-        quant_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16 *)in, len, amax, out);
+        if (vec) GBC_QUANT(__nv_bfloat16, true); else GBC_QUANT(__nv_bfloat16, false);
     } else {
         return GBCONV_ERR_UNSUPPORTED;
     }
+#undef GBC_QUANT
     finalize_scale<<<grid_for(rows, 256), 256, 0, st>>>(amax, rows);
     return cuda_status(cudaGetLastError());
 }

@@ -70,6 +70,7 @@ gbconv_status_t launch_tc_grouped(int count, const Dims *d, const TcConfig *cfg,
                                   const void *const *x, const void *const *w,
                                   const float *const *bias, void *const *y, cudaStream_t st);
 bool tc_wgrad_supported(const Dims &d);
+long long tc_wgrad_pixel_steps(const Dims &d);  // 64-pixel reduction steps
 TcConfig tc_wgrad_default_config(const Dims &d);
 gbconv_status_t launch_tc_wgrad_partials(const Dims &d, const TcConfig &cfg, const void *x,
                                          const void *g, float *ws, cudaStream_t st);

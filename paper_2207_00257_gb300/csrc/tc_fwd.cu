@@ -9,15 +9,19 @@
 // tile of it per filter tap and channel block) and B the KRSC filter.
 //
 // One persistent CTA per SM walks output tiles of 128 pixels x BN channels.
-// Warp roles (192 threads):
-//   warp 0  producer: one thread issues the TMA loads of A (im2col) and B
-//           (tiled) into an S-stage shared-memory ring ("full"/"empty" mbarriers);
+// Warp roles (320 threads):
+//   warp 0  producer: one thread issues the TMA loads of A (im2col, or plain
+//           tiled rows for 1x1 stride-1 unpadded layers) and B (tiled) into an
+//           S-stage shared-memory ring ("full"/"empty" mbarriers);
 //   warp 1  MMA issuer: one thread issues tcgen05.mma (128 x BN x 16 for BF16,
 //           x 32 for E4M3) into one of two TMEM accumulators and commits each
 //           stage back to the producer;
-//   warps 2-5 epilogue: tcgen05.ld of the accumulator, FP8 scales, bias,
-//           ReLU, conversion and 16-byte vector stores, while the MMA warp
-//           fills the other accumulator.
+//   warps 2-9 epilogue: two warps per TMEM lane quarter, alternating 32-column
+//           chunks: tcgen05.ld, FP8 scales and bias (one coalesced load, then
+//           warp shuffles), ReLU, conversion, a swizzled staging buffer in
+//           shared memory and a TMA tensor store of the 32 x 32 chunk. A warp
+//           releases the accumulator right after its last TMEM load, so the
+//           MMA warp refills it while the stores drain.
 // Every mbarrier wait is bounded (ptx::mbar_wait); on a timeout the kernel
 // records DEVERR_TIMEOUT, drains its own in-flight copies and MMAs, frees
 // TMEM and returns.
@@ -38,7 +42,10 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int A_BYTES = BM * 128;  // 128 pixels x 128 bytes of channels
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 320;
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_BYTES = 4096;    // staging buffer per epilogue warp
+constexpr int EPI_TOTAL = EPI_WARPS * EPI_BYTES;
 constexpr int SMEM_ALIGN = 1024;
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -49,17 +56,17 @@ struct ProbArgs {
     int pw, ph, u, v, dh, dw, S, RS;
     int c_blocks, kb_per_tile;
     int n_tiles, bn, K;
-    int relu, out_f32;
+    int relu, out_f32, a_tiled;
     const float *bias;
     const float *x_scale;
     const float *w_scale;
-    void *y;
 };
 
 template <int G>
 struct FwdParams {
     CUtensorMap tmA[G];
     CUtensorMap tmB[G];
+    CUtensorMap tmY[G];
     ProbArgs pa[G];
     int tile_start[G + 1];  // prefix sums of tiles per problem
     int count;
@@ -68,6 +75,11 @@ struct FwdParams {
     int raster;
     Guard guard;
 };
+
+// All per-problem descriptors of a grouped launch travel as kernel parameters
+// (no host-to-device copy, graph-capturable): they must fit the 32764-byte
+// parameter limit.
+static_assert(sizeof(FwdParams<GMAX>) <= 32764, "grouped kernel parameters too large");
 
 template <int BN>
 struct TmemCols {
@@ -98,6 +110,67 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// Epilogue of one 32-row x 32-column accumulator chunk held by a warp (lane =
+// row): scale, bias, ReLU, convert, stage in shared memory in the layout the
+// TMA store's swizzle expects, and store the chunk with one TMA instruction.
+//   BF16 output: 32 rows x 64 B, 64-byte swizzle (16-B unit c of row r sits at
+//                unit c ^ ((r >> 1) & 3)), two 2 KB halves used alternately;
+//   FP32 output: 32 rows x 128 B, 128-byte swizzle (unit c ^ (r & 7)).
+template <bool FP8>
+__device__ __forceinline__ void epilogue_chunk(const uint32_t (&v)[32], const ProbArgs &pa,
+                                               const CUtensorMap *tmY, float xs, int col0,
+                                               int row0, int lane, uint8_t *sbuf, int &ebuf) {
+    float scl = 1.f, bl = 0.f;
+    const int mycol = col0 + lane;
+    if (mycol < pa.K) {
+        if (FP8) scl = xs * __ldg(pa.w_scale + mycol);
+        if (pa.bias) bl = __ldg(pa.bias + mycol);
+    }
+    float f[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        float a = __uint_as_float(v[i]);
+        if (FP8) a = a * __shfl_sync(0xffffffffu, scl, i);
+        if (pa.bias) a = a + __shfl_sync(0xffffffffu, bl, i);
+        if (pa.relu) a = fmaxf(a, 0.f);
+        f[i] = a;
+    }
+    if (pa.out_f32) {
+        if (lane == 0) ptx::bulk_wait_read<0>();
+        __syncwarp();
+        uint8_t *dst = sbuf + lane * 128;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<uint4 *>(dst + ((c ^ (lane & 7)) << 4)) =
+                make_uint4(__float_as_uint(f[4 * c]), __float_as_uint(f[4 * c + 1]),
+                           __float_as_uint(f[4 * c + 2]), __float_as_uint(f[4 * c + 3]));
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            ptx::tma_store_2d(tmY, sbuf, col0, row0);
+            ptx::bulk_commit();
+        }
+    } else {
+        uint8_t *b = sbuf + ebuf * 2048;
+        if (lane == 0) ptx::bulk_wait_read<1>();
+        __syncwarp();
+        uint8_t *dst = b + lane * 64;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(dst + ((c ^ ((lane >> 1) & 3)) << 4)) =
+                make_uint4(pack_bf16(f[8 * c], f[8 * c + 1]), pack_bf16(f[8 * c + 2], f[8 * c + 3]),
+                           pack_bf16(f[8 * c + 4], f[8 * c + 5]),
+                           pack_bf16(f[8 * c + 6], f[8 * c + 7]));
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            ptx::tma_store_2d(tmY, b, col0, row0);
+            ptx::bulk_commit();
+        }
+        ebuf ^= 1;
+    }
+}
+
 template <int BN, bool FP8, int G>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_constant__ FwdParams<G> prm) {
     constexpr int KE = FP8 ? 128 : 64;         // reduction elements per 128-byte row
@@ -111,7 +184,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_consta
     const int stages = prm.stages;
     uint8_t *sA = base;
     uint8_t *sB = base + stages * A_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sB + stages * B_STAGE);
+    uint8_t *sEpi = sB + stages * B_STAGE;  // 1024-aligned: A and B stages are multiples of 1024
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sEpi + EPI_TOTAL);
     uint64_t *full = bars;                // [stages]
     uint64_t *empty = bars + stages;      // [stages]
     uint64_t *tfull = bars + 2 * stages;  // [2]
@@ -130,7 +204,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_consta
         }
         for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(&tfull[i], 1);
-            ptx::mbar_init(&tempty[i], 4);
+            ptx::mbar_init(&tempty[i], EPI_WARPS);
         }
         ptx::mbar_init(done, 1);
         *abort_flag = 0;
@@ -179,9 +253,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_consta
                         }
                         if (!prm.guard.skip_loads) {
                             ptx::mbar_arrive_expect_tx(&full[stage], bytes);
-                            ptx::tma_load_im2col_4d(sA + stage * A_BYTES, ta, &full[stage],
-                                                    cb * KE, wc, hc, n,
-                                                    (uint16_t)(s * pa.dw), (uint16_t)(r * pa.dh));
+                            if (pa.a_tiled)
+                                ptx::tma_load_2d(sA + stage * A_BYTES, ta, &full[stage], cb * KE, m0);
+                            else
+                                ptx::tma_load_im2col_4d(sA + stage * A_BYTES, ta, &full[stage],
+                                                        cb * KE, wc, hc, n, (uint16_t)(s * pa.dw),
+                                                        (uint16_t)(r * pa.dh));
                             ptx::tma_load_3d(sB + stage * B_STAGE, tb, &full[stage], cb * KE, rs,
                                              n0);
                             ++issued;
@@ -267,8 +344,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_consta
         }
     } else {
         // ------------------------------ epilogue ------------------------------
-        const int quarter = warp & 3;  // TMEM lanes this warp may access
-        const int row = quarter * 32 + lane;
+        const int ew = warp - 2;        // 0..7
+        const int quarter = warp & 3;   // TMEM lanes this warp may access
+        const int half = ew >> 2;       // this warp takes chunks j with j % 2 == half
+        uint8_t *sbuf = sEpi + ew * EPI_BYTES;
+        int ebuf = 0;
         int local = 0;
         for (int tile = blockIdx.x; tile < prm.num_tiles; tile += gridDim.x, ++local) {
             int g, mt, nt;
@@ -281,59 +361,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_consta
                 break;
             }
             ptx::tc_fence_after();
-            const long long m = (long long)mt * BM + row;
-            const bool mval = m < pa.M;
+            const int row0 = mt * BM + quarter * 32;
             const float xs = FP8 ? __ldg(pa.x_scale) : 1.f;
             const int nchunks = pa.bn / 32;
-            for (int j = 0; j < nchunks; ++j) {
+            bool released = false;
+            for (int j = half; j < nchunks; j += 2) {
                 uint32_t v[32];
                 ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
                                             (uint32_t)(acc * BN + j * 32),
                                         v);
                 ptx::tmem_ld_wait();
+                if (j + 2 >= nchunks) {  // last TMEM read of this warp for this tile
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+                    released = true;
+                }
                 const int col0 = nt * pa.bn + j * 32;
-                if (!mval || col0 >= pa.K) continue;
-                float f[32];
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    float a = __uint_as_float(v[i]);
-                    const int col = min(col0 + i, pa.K - 1);
-                    if (FP8) a = a * (xs * __ldg(pa.w_scale + col));
-                    if (pa.bias) a = __ldg(pa.bias + col) + a;
-                    if (pa.relu) a = fmaxf(a, 0.f);
-                    f[i] = a;
-                }
-                const bool whole = col0 + 32 <= pa.K;
-                if (pa.out_f32) {
-                    float *yp = reinterpret_cast<float *>(pa.y) + m * pa.K + col0;
-                    if (whole) {
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            reinterpret_cast<float4 *>(yp)[i] =
-                                make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
-                    } else {
-                        for (int i = 0; i < 32 && col0 + i < pa.K; ++i) yp[i] = f[i];
-                    }
-                } else {
-                    __nv_bfloat16 *yp = reinterpret_cast<__nv_bfloat16 *>(pa.y) + m * pa.K + col0;
-                    if (whole) {
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            reinterpret_cast<uint4 *>(yp)[i] =
-                                make_uint4(pack_bf16(f[8 * i], f[8 * i + 1]),
-                                           pack_bf16(f[8 * i + 2], f[8 * i + 3]),
-                                           pack_bf16(f[8 * i + 4], f[8 * i + 5]),
-                                           pack_bf16(f[8 * i + 6], f[8 * i + 7]));
-                    } else {
-                        for (int i = 0; i < 32 && col0 + i < pa.K; ++i)
-                            yp[i] = __float2bfloat16_rn(f[i]);
-                    }
-                }
+                if (col0 >= pa.K || row0 >= pa.M) continue;  // chunk entirely outside y
+                epilogue_chunk<FP8>(v, pa, &prm.tmY[g], xs, col0, row0, lane, sbuf, ebuf);
             }
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+            if (!released) {
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+            }
         }
+        if (lane == 0) ptx::bulk_wait<0>();  // stores done before the CTA leaves
     }
 
     __syncwarp();
@@ -352,12 +406,12 @@ constexpr int b_stage_bytes() { return BN * 128; }
 
 int max_stages(int bn) {
     int per = A_BYTES + bn * 128;
-    int s = (SMEM_LIMIT - SMEM_ALIGN - BAR_BYTES) / per;
+    int s = (SMEM_LIMIT - SMEM_ALIGN - BAR_BYTES - EPI_TOTAL) / per;
     return std::min(s, 12);
 }
 
 size_t smem_bytes(int bn, int stages) {
-    return (size_t)SMEM_ALIGN + (size_t)stages * (A_BYTES + bn * 128) + BAR_BYTES;
+    return (size_t)SMEM_ALIGN + (size_t)stages * (A_BYTES + bn * 128) + EPI_TOTAL + BAR_BYTES;
 }
 
 template <int BN, bool FP8, int G>
@@ -377,11 +431,33 @@ gbconv_status_t launch_kernel(const FwdParams<G> &prm, int grid, cudaStream_t st
 // Fills pa, tmA, tmB for one problem; bn is the tile width used.
 gbconv_status_t setup_problem(const Dims &d, int bn, const void *x, const void *w,
                               const float *bias, const float *x_scale, const float *w_scale,
-                              void *y, ProbArgs &pa, CUtensorMap &ta, CUtensorMap &tb) {
+                              void *y, ProbArgs &pa, CUtensorMap &ta, CUtensorMap &tb,
+                              CUtensorMap &ty) {
     const bool fp8 = d.in_dtype == GBCONV_E4M3;
     const int eb = fp8 ? 1 : 2;
     const int ke = 128 / eb;
-    gbconv_status_t s = encode_im2col_act(&ta, d, x, eb, ke, BM);
+    const CUtensorMapDataType in_t =
+        fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    // A 1x1, stride-1, unpadded convolution reads x as the plain matrix [N*H*W][C].
+    const bool a_tiled = d.R == 1 && d.S == 1 && d.u == 1 && d.v == 1 && d.ph == 0 && d.pw == 0;
+    gbconv_status_t s;
+    if (a_tiled) {
+        uint64_t adims[2] = {(uint64_t)d.C, (uint64_t)d.M()};
+        uint64_t astr[1] = {(uint64_t)d.C * eb};
+        uint32_t abox[2] = {(uint32_t)ke, (uint32_t)BM};
+        s = encode_tiled(&ta, in_t, 2, x, adims, astr, abox, CU_TENSOR_MAP_SWIZZLE_128B);
+    } else {
+        s = encode_im2col_act(&ta, d, x, eb, ke, BM);
+    }
+    if (s != GBCONV_OK) return s;
+    // y [M][K]: stored in 32-row x 32-column chunks (BF16: 64-byte rows, FP32: 128-byte rows)
+    const bool of32 = d.out_dtype == GBCONV_F32;
+    uint64_t ydims[2] = {(uint64_t)d.K, (uint64_t)d.M()};
+    uint64_t ystr[1] = {(uint64_t)d.K * (of32 ? 4 : 2)};
+    uint32_t ybox[2] = {32, 32};
+    s = encode_tiled(&ty, of32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                     2, y, ydims, ystr, ybox,
+                     of32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
     if (s != GBCONV_OK) return s;
     uint64_t dims[3] = {(uint64_t)d.C, (uint64_t)d.R * d.S, (uint64_t)d.K};
     uint64_t strides[2] = {(uint64_t)d.C * eb, (uint64_t)d.R * d.S * d.C * eb};
@@ -406,11 +482,11 @@ gbconv_status_t setup_problem(const Dims &d, int bn, const void *x, const void *
     pa.bn = bn;
     pa.K = d.K;
     pa.relu = (d.flags & GBCONV_FLAG_RELU) ? 1 : 0;
-    pa.out_f32 = d.out_dtype == GBCONV_F32;
+    pa.out_f32 = of32;
+    pa.a_tiled = a_tiled;
     pa.bias = (d.flags & GBCONV_FLAG_BIAS) ? bias : nullptr;
     pa.x_scale = x_scale;
     pa.w_scale = w_scale;
-    pa.y = y;
     return GBCONV_OK;
 }
 
@@ -465,7 +541,7 @@ gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void 
     FwdParams<1> prm;
     memset(&prm, 0, sizeof(prm));
     gbconv_status_t s = setup_problem(d, cfg.block_n, x, w, bias, x_scale, w_scale, y, prm.pa[0],
-                                      prm.tmA[0], prm.tmB[0]);
+                                      prm.tmA[0], prm.tmB[0], prm.tmY[0]);
     if (s != GBCONV_OK) return s;
     prm.count = 1;
     prm.tile_start[0] = 0;
@@ -514,7 +590,7 @@ gbconv_status_t launch_tc_grouped(int count, const Dims *d, const TcConfig *cfg,
                 return GBCONV_ERR_INVALID_ARG;
             gbconv_status_t s = setup_problem(d[i], cfg[i].block_n, x[i], w[i], bias[i], nullptr,
                                               nullptr, y[i], prm.pa[slot], prm.tmA[slot],
-                                              prm.tmB[slot]);
+                                              prm.tmB[slot], prm.tmY[slot]);
             if (s != GBCONV_OK) return s;
             prm.tile_start[slot] = tiles;
             tiles += tiles_of(prm.pa[slot]);

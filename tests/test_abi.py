@@ -136,7 +136,7 @@ def test_workspace_sizes():
     s, n = B.gbconv_workspace_size(B.GBCONV_OP_WGRAD, p)
     s2, cfg = B.gbconv_get_config(B.GBCONV_OP_WGRAD, p)
     assert s == s2 == B.GBCONV_OK and cfg.split_k >= 1
-    assert n >= cfg.split_k * (128 * 128 * 9 + 128) * 4
+    assert n >= (cfg.split_k * 128 * 128 * 9 + 128 * 128) * 4
     # too small a workspace is refused before anything runs
     assert B.conv2d_wgrad(p, 4096, 8192, 12288, 0, 16384, n - 256, 0) == B.GBCONV_ERR_WORKSPACE
     assert B.conv2d_dgrad(p, 4096, 8192, 12288, 16384, 16, 0) == B.GBCONV_ERR_WORKSPACE

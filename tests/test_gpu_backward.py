@@ -160,3 +160,49 @@ def test_autograd_fp32_nchw():
     dwr, dwb = oracle.conv2d_wgrad(p, f64(x), f64(g), with_bound=True)
     assert oracle.max_normalised_error(f64(xg.grad), dxr, dxb) <= TOL_F32
     assert oracle.max_normalised_error(f64(wg.grad), dwr, dwb) <= TOL_F32
+
+
+# ---- tensor-core weight gradient (BF16 NHWC, C % 64 == 0) ----
+
+TC_WGRAD_SHAPES = [
+    ConvShape(2, 64, 9, 11, 64, 3, 3, 1, 1, 1),
+    ConvShape(3, 128, 12, 12, 72, 3, 3, 2, 1, 1),     # partial output-channel tile, stride 2
+    ConvShape(1, 64, 15, 13, 200, 3, 3, 1, 2, 2),     # two output-channel tiles, dilation 2
+    ConvShape(2, 256, 7, 7, 64, 1, 1, 1, 0, 1),       # 256-channel tile, 1x1
+    ConvShape(2, 192, 10, 10, 32, 5, 5, 1, 2, 1),     # 64-channel tiles, 5x5
+    ConvShape(1, 64, 5, 5, 16, 3, 3, 1, 1, 1),        # fewer pixels than one 64-pixel step
+]
+
+
+@pytest.mark.parametrize("sh", TC_WGRAD_SHAPES, ids=_id)
+def test_tc_wgrad_shapes(sh):
+    e = _grads(sh, torch.bfloat16, seed=60)
+    assert e["dw"] <= TOL_ACC32 and e["db"] <= TOL_ACC32, e
+
+
+@pytest.mark.parametrize("split", [1, 5, 16])
+def test_tc_wgrad_split_values(split):
+    sh = ConvShape(4, 128, 14, 14, 128, 3, 3, 1, 1, 1)
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, 1, 1, 1, B.GBCONV_BF16,
+                     B.GBCONV_BF16)
+    B.check(B.gbconv_set_config(B.GBCONV_OP_WGRAD, prob, B.gbconv_config_t(0, 0, split, 0)),
+            "set_config")
+    try:
+        e = _grads(sh, torch.bfloat16, seed=61)
+    finally:
+        B.gbconv_shutdown()
+    assert e["dw"] <= TOL_ACC32 and e["db"] <= TOL_ACC32, e
+
+
+def test_tc_wgrad_integer_exact():
+    """Integer x and g: all partial sums are integers below 2^24, so the
+    tensor-core partials and the compensated slice sum are exact."""
+    sh = ConvShape(2, 64, 10, 10, 96, 3, 3, 1, 1, 1)
+    x, w, b, g = make_inputs(sh, 62, x_dist=("int", -4, 4), w_dist=("int", -4, 4), grad=True)
+    g = torch.randint(-4, 5, g.shape, generator=torch.Generator().manual_seed(63)).float()
+    xb, gb = x.bfloat16().cuda(), g.bfloat16().cuda()
+    dw, db = F.conv2d_wgrad(xb, gb, tuple(w.shape), 1, 1, 1)
+    F.device_error()
+    p = oconv(sh)
+    assert np.array_equal(f64(dw), oracle.conv2d_wgrad(p, f64(x), f64(g)))
+    assert np.array_equal(f64(db), oracle.conv2d_bgrad(p, f64(g)))
