@@ -88,12 +88,19 @@ typedef struct {
  * hand). block_n: output-channel tile (32..256, tensor-core paths) ; stages:
  * shared-memory pipeline depth; split_k: number of slices the reduction is
  * cut into (wgrad); raster: 0 = output-channel tiles fastest, 1 = pixel tiles
- * fastest. A zero field means "library default". */
+ * fastest; algo (tensor-core forward and data gradient): GBCONV_ALGO_AUTO,
+ * GBCONV_ALGO_IM2COL (one TMA im2col tile per filter tap) or
+ * GBCONV_ALGO_SHIFT (stride 1 only: one input band per channel block, filter
+ * taps as row shifts of it). A zero field means "library default". */
+#define GBCONV_ALGO_AUTO 0
+#define GBCONV_ALGO_IM2COL 1
+#define GBCONV_ALGO_SHIFT 2
 typedef struct {
     int32_t block_n;
     int32_t stages;
     int32_t split_k;
     int32_t raster;
+    int32_t algo;
 } gbconv_config_t;
 
 /* A CUDA stream (cudaStream_t). NULL means the legacy default stream. */

@@ -398,6 +398,7 @@ gbconv_status_t gbconv_get_config(int32_t op, const gbconv_problem_t *prob, gbco
     cfg->stages = c.stages;
     cfg->split_k = c.split_k;
     cfg->raster = c.raster;
+    cfg->algo = c.algo;
     return GBCONV_OK;
 }
 
@@ -411,13 +412,14 @@ gbconv_status_t gbconv_set_config(int32_t op, const gbconv_problem_t *prob,
         cfg->block_n != 256)
         return GBCONV_ERR_INVALID_ARG;
     if (cfg->split_k < 0 || cfg->split_k > 1024 || cfg->stages < 0 || cfg->raster < 0 ||
-        cfg->raster > 1)
+        cfg->raster > 1 || cfg->algo < GBCONV_ALGO_AUTO || cfg->algo > GBCONV_ALGO_SHIFT)
         return GBCONV_ERR_INVALID_ARG;
     TcConfig c = config_for(op, *prob, d);  // defaults for zero fields
     if (cfg->block_n) c.block_n = cfg->block_n;
     if (cfg->stages) c.stages = cfg->stages;
     if (cfg->split_k) c.split_k = cfg->split_k;
     c.raster = cfg->raster;
+    c.algo = cfg->algo;
     std::string k = problem_key(op, *prob);
     std::lock_guard<std::mutex> lock(g_mu);
     g_tune[k] = c;
@@ -448,12 +450,16 @@ gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void
         if (tc) {
             for (int bn : {32, 64, 128, 256}) {
                 if (bn > 32 && bn / 2 >= kout) continue;  // wider than needed
-                for (int raster : {0, 1}) {
-                    TcConfig c = base;
-                    c.block_n = bn;
-                    c.stages = 0;  // maximum for this width
-                    c.raster = raster;
-                    cands.push_back(c);
+                for (int algo : {GBCONV_ALGO_IM2COL, GBCONV_ALGO_SHIFT}) {
+                    if (algo == GBCONV_ALGO_SHIFT && !tc_fwd_shift_supported(t, bn)) continue;
+                    for (int raster : {0, 1}) {
+                        TcConfig c = base;
+                        c.block_n = bn;
+                        c.stages = 0;  // maximum for this width
+                        c.raster = raster;
+                        c.algo = algo;
+                        cands.push_back(c);
+                    }
                 }
             }
         } else {
@@ -500,6 +506,7 @@ gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void
         best->stages = best_c.stages;
         best->split_k = best_c.split_k;
         best->raster = best_c.raster;
+        best->algo = best_c.algo;
     }
     return gbconv_get_device_error(stream);
 }
@@ -512,9 +519,11 @@ gbconv_status_t gbconv_tune_cache_save(const char *path) {
     fprintf(f, "{\"version\": %d, \"entries\": [\n", 10000);
     bool first = true;
     for (auto &kv : g_tune) {
-        fprintf(f, "%s {\"key\": \"%s\", \"block_n\": %d, \"stages\": %d, \"split_k\": %d, \"raster\": %d}",
+        fprintf(f,
+                "%s {\"key\": \"%s\", \"block_n\": %d, \"stages\": %d, \"split_k\": %d, "
+                "\"raster\": %d, \"algo\": %d}",
                 first ? "" : ",\n", kv.first.c_str(), kv.second.block_n, kv.second.stages,
-                kv.second.split_k, kv.second.raster);
+                kv.second.split_k, kv.second.raster, kv.second.algo);
         first = false;
     }
     fprintf(f, "\n]}\n");
@@ -536,8 +545,10 @@ gbconv_status_t gbconv_tune_cache_load(const char *path) {
         const char *ke = strchr(k, '"');
         if (!ke) continue;
         TcConfig c{};
-        if (sscanf(ke, "\", \"block_n\": %d, \"stages\": %d, \"split_k\": %d, \"raster\": %d",
-                   &c.block_n, &c.stages, &c.split_k, &c.raster) != 4) {
+        if (sscanf(ke,
+                   "\", \"block_n\": %d, \"stages\": %d, \"split_k\": %d, \"raster\": %d, "
+                   "\"algo\": %d",
+                   &c.block_n, &c.stages, &c.split_k, &c.raster, &c.algo) != 5) {
             fclose(f);
             return GBCONV_ERR_INVALID_ARG;
         }

@@ -9,6 +9,8 @@
 #include <cuda_fp8.h>
 
 #include "internal.h"
+#include "launch.cuh"
+#include "ptx.cuh"
 
 namespace gbc {
 namespace {
@@ -26,6 +28,8 @@ __device__ __forceinline__ void neumaier(float &sum, float &comp, float v) {
 
 __global__ void reduce_slices_kernel(const float *__restrict__ ws, int slices, long long n,
                                      float *__restrict__ out) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         float sum = 0.f, comp = 0.f;
@@ -48,6 +52,8 @@ __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return _
 template <typename T>
 __global__ void __launch_bounds__(256) bias_grad_nhwc(const T *__restrict__ g, long long M, int K,
                                                       int slices, float *__restrict__ part) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
     __shared__ float sh[8][33];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int k = blockIdx.x * 32 + lane;
@@ -79,6 +85,8 @@ __global__ void __launch_bounds__(256) bias_grad_nhwc(const T *__restrict__ g, l
 template <typename T>
 __global__ void bias_grad_nchw(const T *__restrict__ g, int N, int K, long long PQ, int slices,
                                float *__restrict__ part) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
     __shared__ float sh[256];
     const int k = blockIdx.x;
     int n0 = (int)((long long)N * blockIdx.y / slices), n1 = (int)((long long)N * (blockIdx.y + 1) / slices);
@@ -100,6 +108,8 @@ __global__ void bias_grad_nchw(const T *__restrict__ g, int N, int K, long long 
 template <typename T>
 __global__ void rotate_krsc(const T *__restrict__ w, T *__restrict__ wr, int K, int R, int S,
                             int C) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
     long long total = (long long)K * R * S * C;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -136,6 +146,8 @@ __device__ __forceinline__ void load8(const __nv_bfloat16 *p, float (&v)[8]) {
 // aligned groups), else one value per step.
 template <typename T, bool VEC>
 __global__ void amax_kernel(const T *__restrict__ in, long long len, unsigned *__restrict__ amax_bits) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
     __shared__ float sh[256];
     const T *g = in + (long long)blockIdx.y * len;
     float m = 0.f;
@@ -173,6 +185,8 @@ __device__ __forceinline__ uint8_t e4m3_of(float v, float s) {
 template <typename T, bool VEC>
 __global__ void quant_kernel(const T *__restrict__ in, long long len,
                              const unsigned *__restrict__ amax_bits, uint8_t *__restrict__ out) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
     const long long base = (long long)blockIdx.y * len;
     const float s = scale_of(amax_bits[blockIdx.y]);
     if (VEC) {
@@ -196,6 +210,8 @@ __global__ void quant_kernel(const T *__restrict__ in, long long len,
 }
 
 __global__ void finalize_scale(unsigned *__restrict__ amax_bits, long long rows) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
          r += (long long)gridDim.x * blockDim.x) {
         float s = scale_of(amax_bits[r]);
@@ -216,44 +232,48 @@ unsigned grid_for(long long n, int block, int per_sm = 8) {
 gbconv_status_t launch_reduce_slices(const float *ws, int slices, long long n, float *out,
                                      cudaStream_t st) {
     if (n <= 0) return GBCONV_OK;
-    reduce_slices_kernel<<<grid_for(n, 256), 256, 0, st>>>(ws, slices, n, out);
-    return cuda_status(cudaGetLastError());
+    return cuda_status(
+        launch_pdl(reduce_slices_kernel, dim3(grid_for(n, 256)), dim3(256), 0, st, ws, slices, n, out));
 }
 
 gbconv_status_t launch_bias_grad(const Dims &d, const void *g, float *db, float *ws, int slices,
                                  cudaStream_t st) {
+    cudaError_t e;
     if (d.layout == GBCONV_NHWC) {
         dim3 grid((unsigned)((d.K + 31) / 32), (unsigned)slices);
         if (d.in_dtype == GBCONV_F32)
-            bias_grad_nhwc<float><<<grid, 256, 0, st>>>((const float *)g, d.M(), d.K, slices, ws);
+            e = launch_pdl(bias_grad_nhwc<float>, grid, dim3(256), 0, st, (const float *)g, d.M(), d.K,
+                           slices, ws);
         else
-            bias_grad_nhwc<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16 *)g, d.M(),
-                                                                d.K, slices, ws);
+            e = launch_pdl(bias_grad_nhwc<__nv_bfloat16>, grid, dim3(256), 0, st,
+                           (const __nv_bfloat16 *)g, d.M(), d.K, slices, ws);
     } else {
         dim3 grid((unsigned)d.K, (unsigned)slices);
         long long PQ = (long long)d.P * d.Q;
         if (d.in_dtype == GBCONV_F32)
-            bias_grad_nchw<float><<<grid, 256, 0, st>>>((const float *)g, d.N, d.K, PQ, slices, ws);
+            e = launch_pdl(bias_grad_nchw<float>, grid, dim3(256), 0, st, (const float *)g, d.N, d.K,
+                           PQ, slices, ws);
         else
-            bias_grad_nchw<__nv_bfloat16><<<grid, 256, 0, st>>>((const __nv_bfloat16 *)g, d.N, d.K,
-                                                                PQ, slices, ws);
+            e = launch_pdl(bias_grad_nchw<__nv_bfloat16>, grid, dim3(256), 0, st,
+                           (const __nv_bfloat16 *)g, d.N, d.K, PQ, slices, ws);
     }
-    gbconv_status_t s = cuda_status(cudaGetLastError());
-    if (s != GBCONV_OK) return s;
+    if (e != cudaSuccess) return cuda_status(e);
     return launch_reduce_slices(ws, slices, d.K, db, st);
 }
 
 gbconv_status_t launch_rotate_filter(const Dims &d, const void *w, void *w_rot, cudaStream_t st) {
     long long total = (long long)d.K * d.R * d.S * d.C;
     unsigned g = grid_for(total, 256);
+    cudaError_t e;
     if (d.in_dtype == GBCONV_BF16)
-        rotate_krsc<__nv_bfloat16><<<g, 256, 0, st>>>((const __nv_bfloat16 *)w,
-                                                      (__nv_bfloat16 *)w_rot, d.K, d.R, d.S, d.C);
+        e = launch_pdl(rotate_krsc<__nv_bfloat16>, dim3(g), dim3(256), 0, st,
+                       (const __nv_bfloat16 *)w, (__nv_bfloat16 *)w_rot, d.K, d.R, d.S, d.C);
     else if (d.in_dtype == GBCONV_F32)
-        rotate_krsc<float><<<g, 256, 0, st>>>((const float *)w, (float *)w_rot, d.K, d.R, d.S, d.C);
+        e = launch_pdl(rotate_krsc<float>, dim3(g), dim3(256), 0, st, (const float *)w,
+                       (float *)w_rot, d.K, d.R, d.S, d.C);
     else
         return GBCONV_ERR_UNSUPPORTED;
-    return cuda_status(cudaGetLastError());
+    return cuda_status(e);
 }
 
 gbconv_status_t launch_quantize_e4m3(const void *in, int in_dtype, long long rows, long long len,
@@ -273,8 +293,10 @@ gbconv_status_t launch_quantize_e4m3(const void *in, int in_dtype, long long row
     dim3 grid(gx, (unsigned)rows);
 #define GBC_QUANT(T, V)                                                                  \
     do {                                                                               \
-        amax_kernel<T, V><<<grid, 256, 0, st>>>((const T *)in, len, amax);             \
-        quant_kernel<T, V><<<grid, 256, 0, st>>>((const T *)in, len, amax, out);       \
+        e = launch_pdl(amax_kernel<T, V>, grid, dim3(256), 0, st, (const T *)in, len, amax); \
+        if (e == cudaSuccess)                                                          \
+            e = launch_pdl(quant_kernel<T, V>, grid, dim3(256), 0, st, (const T *)in, len, \
+                           (const unsigned *)amax, out);                               \
     } while (0)
     if (in_dtype == GBCONV_F32) {
         if (vec) GBC_QUANT(float, true); else GBC_QUANT(float, false);
@@ -284,8 +306,9 @@ gbconv_status_t launch_quantize_e4m3(const void *in, int in_dtype, long long row
         return GBCONV_ERR_UNSUPPORTED;
     }
 #undef GBC_QUANT
-    finalize_scale<<<grid_for(rows, 256), 256, 0, st>>>(amax, rows);
-    return cuda_status(cudaGetLastError());
+    if (e == cudaSuccess)
+        e = launch_pdl(finalize_scale, dim3(grid_for(rows, 256)), dim3(256), 0, st, amax, rows);
+    return cuda_status(e);
 }
 
 }  // namespace gbc

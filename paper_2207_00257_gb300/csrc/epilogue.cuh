@@ -1,0 +1,98 @@
+// epilogue.cuh -- shared epilogue of the tensor-core forward kernels: one
+// 32 x 32 accumulator chunk from TMEM registers to y through a swizzled
+// shared-memory buffer and a TMA tensor store.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace gbc {
+
+// What the epilogue needs to know about the output.
+struct EpiArgs {
+    int K;                 // output channels (columns >= K are never stored)
+    int relu, out_f32;
+    const float *bias;     // [K] or null
+    const float *w_scale;  // [K] FP8 per-channel scales (FP8 only)
+};
+
+__device__ __forceinline__ void store_chunk(const CUtensorMap *map, const void *src, int c0, int c1,
+                                            int c2) {
+    if (c2 < 0)
+        ptx::tma_store_2d(map, src, c0, c1);
+    else
+        ptx::tma_store_3d(map, src, c0, c1, c2);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // a -> low half
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// Epilogue of one 32-row x 32-column accumulator chunk held by a warp (lane =
+// row): scale, bias, ReLU, convert, stage in shared memory in the layout the
+// TMA store's swizzle expects, and store the chunk with one TMA instruction
+// at coordinates (col0, c1) of a 2-D map, or (col0, c1, c2) of a 3-D map when
+// c2 >= 0.
+//   BF16 output: 32 rows x 64 B, 64-byte swizzle (16-B unit c of row r sits at
+//                unit c ^ ((r >> 1) & 3)), two 2 KB halves used alternately;
+//   FP32 output: 32 rows x 128 B, 128-byte swizzle (unit c ^ (r & 7)).
+template <bool FP8>
+__device__ __forceinline__ void epilogue_chunk(const uint32_t (&v)[32], const EpiArgs &pa,
+                                               const CUtensorMap *tmY, float xs, int col0,
+                                               int c1, int c2, int lane, uint8_t *sbuf, int &ebuf) {
+    float scl = 1.f, bl = 0.f;
+    const int mycol = col0 + lane;
+    if (mycol < pa.K) {
+        if (FP8) scl = xs * __ldg(pa.w_scale + mycol);
+        if (pa.bias) bl = __ldg(pa.bias + mycol);
+    }
+    float f[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        float a = __uint_as_float(v[i]);
+        if (FP8) a = a * __shfl_sync(0xffffffffu, scl, i);
+        if (pa.bias) a = a + __shfl_sync(0xffffffffu, bl, i);
+        if (pa.relu) a = fmaxf(a, 0.f);
+        f[i] = a;
+    }
+    if (pa.out_f32) {
+        if (lane == 0) ptx::bulk_wait_read<0>();
+        __syncwarp();
+        uint8_t *dst = sbuf + lane * 128;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<uint4 *>(dst + ((c ^ (lane & 7)) << 4)) =
+                make_uint4(__float_as_uint(f[4 * c]), __float_as_uint(f[4 * c + 1]),
+                           __float_as_uint(f[4 * c + 2]), __float_as_uint(f[4 * c + 3]));
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            store_chunk(tmY, sbuf, col0, c1, c2);
+            ptx::bulk_commit();
+        }
+    } else {
+        uint8_t *b = sbuf + ebuf * 2048;
+        if (lane == 0) ptx::bulk_wait_read<1>();
+        __syncwarp();
+        uint8_t *dst = b + lane * 64;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(dst + ((c ^ ((lane >> 1) & 3)) << 4)) =
+                make_uint4(pack_bf16(f[8 * c], f[8 * c + 1]), pack_bf16(f[8 * c + 2], f[8 * c + 3]),
+                           pack_bf16(f[8 * c + 4], f[8 * c + 5]),
+                           pack_bf16(f[8 * c + 6], f[8 * c + 7]));
+        ptx::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            store_chunk(tmY, b, col0, c1, c2);
+            ptx::bulk_commit();
+        }
+        ebuf ^= 1;
+    }
+}
+
+
+}  // namespace gbc

@@ -60,12 +60,18 @@ struct TcConfig {
     int stages;
     int split_k;   // wgrad slices
     int raster;    // 0: output-channel tiles fastest
+    int algo;      // GBCONV_ALGO_*
 };
 bool tc_fwd_supported(const Dims &d);
 TcConfig tc_fwd_default_config(const Dims &d);
 gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg, const void *x, const void *w,
                               const float *bias, const float *x_scale, const float *w_scale,
                               void *y, cudaStream_t st);
+// tc_fwd_shift.cu: stride-1 layers, one input band per channel block.
+bool tc_fwd_shift_supported(const Dims &d, int block_n);
+gbconv_status_t launch_tc_fwd_shift(const Dims &d, const TcConfig &cfg, const void *x,
+                                    const void *w, const float *bias, const float *x_scale,
+                                    const float *w_scale, void *y, cudaStream_t st);
 gbconv_status_t launch_tc_grouped(int count, const Dims *d, const TcConfig *cfg,
                                   const void *const *x, const void *const *w,
                                   const float *const *bias, void *const *y, cudaStream_t st);

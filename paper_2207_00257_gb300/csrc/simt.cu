@@ -15,6 +15,8 @@
 #include <cuda_bf16.h>
 
 #include "internal.h"
+#include "launch.cuh"
+#include "ptx.cuh"
 
 namespace gbc {
 namespace {
@@ -64,6 +66,7 @@ __global__ void __launch_bounds__(NT) simt_igemm(L ldr) {
     __shared__ __align__(16) float Bs[2][BK][BN + BPAD];
     const int t = threadIdx.x;
     const int tm = t % 16, tn = t / 16;
+    ptx::griddep_wait();
     ldr.begin(t);
     const int k0 = ldr.kt_begin(), k1 = ldr.kt_end();
     float acc[8][4];
@@ -116,6 +119,7 @@ __global__ void __launch_bounds__(NT) simt_igemm(L ldr) {
         __syncthreads();
         buf ^= 1;
     }
+    if (t == 0) ptx::griddep_launch();
     ldr.epilogue(acc, tm, tn);
 }
 
@@ -421,8 +425,7 @@ struct WgradLoader {
 template <class L>
 gbconv_status_t launch(const L &ldr, dim3 grid, cudaStream_t st) {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return GBCONV_OK;
-    simt_igemm<L><<<grid, NT, 0, st>>>(ldr);
-    return cuda_status(cudaGetLastError());
+    return cuda_status(launch_pdl(simt_igemm<L>, grid, dim3(NT), 0, st, ldr));
 }
 
 template <typename Ti, typename To>

@@ -34,7 +34,9 @@
 #include <mutex>
 #include <vector>
 
+#include "epilogue.cuh"
 #include "internal.h"
+#include "launch.cuh"
 #include "ptx.cuh"
 
 namespace gbc {
@@ -105,72 +107,6 @@ __device__ __forceinline__ void decode(const FwdParams<G> &prm, int tile, int &g
     }
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // a -> low half
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
-// Epilogue of one 32-row x 32-column accumulator chunk held by a warp (lane =
-// row): scale, bias, ReLU, convert, stage in shared memory in the layout the
-// TMA store's swizzle expects, and store the chunk with one TMA instruction.
-//   BF16 output: 32 rows x 64 B, 64-byte swizzle (16-B unit c of row r sits at
-//                unit c ^ ((r >> 1) & 3)), two 2 KB halves used alternately;
-//   FP32 output: 32 rows x 128 B, 128-byte swizzle (unit c ^ (r & 7)).
-template <bool FP8>
-__device__ __forceinline__ void epilogue_chunk(const uint32_t (&v)[32], const ProbArgs &pa,
-                                               const CUtensorMap *tmY, float xs, int col0,
-                                               int row0, int lane, uint8_t *sbuf, int &ebuf) {
-    float scl = 1.f, bl = 0.f;
-    const int mycol = col0 + lane;
-    if (mycol < pa.K) {
-        if (FP8) scl = xs * __ldg(pa.w_scale + mycol);
-        if (pa.bias) bl = __ldg(pa.bias + mycol);
-    }
-    float f[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        float a = __uint_as_float(v[i]);
-        if (FP8) a = a * __shfl_sync(0xffffffffu, scl, i);
-        if (pa.bias) a = a + __shfl_sync(0xffffffffu, bl, i);
-        if (pa.relu) a = fmaxf(a, 0.f);
-        f[i] = a;
-    }
-    if (pa.out_f32) {
-        if (lane == 0) ptx::bulk_wait_read<0>();
-        __syncwarp();
-        uint8_t *dst = sbuf + lane * 128;
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            *reinterpret_cast<uint4 *>(dst + ((c ^ (lane & 7)) << 4)) =
-                make_uint4(__float_as_uint(f[4 * c]), __float_as_uint(f[4 * c + 1]),
-                           __float_as_uint(f[4 * c + 2]), __float_as_uint(f[4 * c + 3]));
-        ptx::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-            ptx::tma_store_2d(tmY, sbuf, col0, row0);
-            ptx::bulk_commit();
-        }
-    } else {
-        uint8_t *b = sbuf + ebuf * 2048;
-        if (lane == 0) ptx::bulk_wait_read<1>();
-        __syncwarp();
-        uint8_t *dst = b + lane * 64;
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            *reinterpret_cast<uint4 *>(dst + ((c ^ ((lane >> 1) & 3)) << 4)) =
-                make_uint4(pack_bf16(f[8 * c], f[8 * c + 1]), pack_bf16(f[8 * c + 2], f[8 * c + 3]),
-                           pack_bf16(f[8 * c + 4], f[8 * c + 5]),
-                           pack_bf16(f[8 * c + 6], f[8 * c + 7]));
-        ptx::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) {
-            ptx::tma_store_2d(tmY, b, col0, row0);
-            ptx::bulk_commit();
-        }
-        ebuf ^= 1;
-    }
-}
-
 template <int BN, bool FP8, int G>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_constant__ FwdParams<G> prm) {
     constexpr int KE = FP8 ? 128 : 64;         // reduction elements per 128-byte row
@@ -218,6 +154,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_consta
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // Prologue done: now wait for the kernels this one depends on, and let the
+    // next kernel on the stream start launching.
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
 
     auto fail = [&]() {
         *abort_flag = 1;
@@ -379,7 +319,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_consta
                 }
                 const int col0 = nt * pa.bn + j * 32;
                 if (col0 >= pa.K || row0 >= pa.M) continue;  // chunk entirely outside y
-                epilogue_chunk<FP8>(v, pa, &prm.tmY[g], xs, col0, row0, lane, sbuf, ebuf);
+                epilogue_chunk<FP8>(v, EpiArgs{pa.K, pa.relu, pa.out_f32, pa.bias, pa.w_scale},
+                                    &prm.tmY[g], xs, col0, row0, -1, lane, sbuf, ebuf);
             }
             if (!released) {
                 ptx::tc_fence_before();
@@ -424,8 +365,7 @@ gbconv_status_t launch_kernel(const FwdParams<G> &prm, int grid, cudaStream_t st
     });
     if (attr_err != cudaSuccess) return cuda_status(attr_err);
     size_t smem = smem_bytes(BN, prm.stages);
-    tc_fwd_kernel<BN, FP8, G><<<grid, NTHREADS, smem, st>>>(prm);
-    return cuda_status(cudaGetLastError());
+    return cuda_status(launch_pdl(tc_fwd_kernel<BN, FP8, G>, dim3(grid), dim3(NTHREADS), smem, st, prm));
 }
 
 // Fills pa, tmA, tmB for one problem; bn is the tile width used.
@@ -527,6 +467,7 @@ TcConfig tc_fwd_default_config(const Dims &d) {
     c.stages = max_stages(c.block_n);
     c.split_k = 1;
     c.raster = 0;
+    c.algo = GBCONV_ALGO_AUTO;
     return c;
 }
 
@@ -536,6 +477,14 @@ gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void 
     TcConfig cfg = cfg_in;
     if (cfg.block_n != 32 && cfg.block_n != 64 && cfg.block_n != 128 && cfg.block_n != 256)
         return GBCONV_ERR_INVALID_ARG;
+    // Automatic choice: the shifted-band kernel for stride-1 layers with more
+    // than one filter tap (a 1x1 layer gains nothing from it and would compute
+    // the extended rows' spare columns).
+    const bool want_shift = cfg.algo == GBCONV_ALGO_SHIFT ||
+                            (cfg.algo == GBCONV_ALGO_AUTO && d.R * d.S > 1);
+    if (want_shift && tc_fwd_shift_supported(d, cfg.block_n))
+        return launch_tc_fwd_shift(d, cfg, x, w, bias, x_scale, w_scale, y, st);
+    if (cfg.algo == GBCONV_ALGO_SHIFT) return GBCONV_ERR_UNSUPPORTED;
     if (cfg.stages < 2 || cfg.stages > max_stages(cfg.block_n)) cfg.stages = max_stages(cfg.block_n);
     if (d.M() == 0) return GBCONV_OK;
     FwdParams<1> prm;

@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "launch.cuh"
 #include "ptx.cuh"
 
 namespace gbc {
@@ -108,6 +109,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_wgrad_kernel(const __grid_cons
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // Prologue done: now wait for the kernels this one depends on, and let the
+    // next kernel on the stream start launching.
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
 
     auto fail = [&]() {
         *abort_flag = 1;
@@ -300,8 +305,8 @@ gbconv_status_t launch(const WgParams &prm, int grid, cudaStream_t st) {
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     });
     if (attr_err != cudaSuccess) return cuda_status(attr_err);
-    tc_wgrad_kernel<BN><<<grid, NTHREADS, smem_bytes(BN, prm.stages), st>>>(prm);
-    return cuda_status(cudaGetLastError());
+    return cuda_status(launch_pdl(tc_wgrad_kernel<BN>, dim3(grid), dim3(NTHREADS),
+                                  smem_bytes(BN, prm.stages), st, prm));
 }
 
 int pick_bn(int C) {

@@ -242,3 +242,45 @@ def test_fp8_full_size_sampled():
     r = fp8_case(sh, seed=12, idx=idx)
     assert r["err_i"] <= TOL_BF16_OUT, r["err_i"]
     assert r["err_ii"] <= TOL_FP8, r["err_ii"]
+
+
+# ---------------- both forward algorithms on the same layers ----------------
+
+ALGO_SHAPES = [
+    ConvShape(2, 64, 9, 11, 64, 3, 3, 1, 1, 1),
+    ConvShape(1, 16, 15, 13, 48, 3, 3, 1, 2, 2),
+    ConvShape(2, 72, 10, 10, 40, 5, 5, 1, 2, 1),
+    ConvShape(2, 64, 30, 60, 96, 3, 3, 1, 1, 1),       # Wx = 64 ... 128 boundary (Q + 2 = 62)
+    ConvShape(1, 64, 6, 100, 64, 3, 3, 1, 1, 1),       # Wx = 128 (Q + 2 = 102), one row per tile
+    ConvShape(2, 32, 7, 7, 32, 1, 1, 1, 0, 1),         # 1x1 forced onto the band kernel
+    ConvShape(3, 64, 9, 9, 64, 3, 5, 1, (1, 2), 1),    # rectangular filter
+]
+
+
+@pytest.mark.parametrize("sh", ALGO_SHAPES, ids=_id)
+@pytest.mark.parametrize("algo", [B.GBCONV_ALGO_IM2COL, B.GBCONV_ALGO_SHIFT])
+@pytest.mark.parametrize("block_n", [64, 128])
+def test_bf16_forward_algorithms(sh, algo, block_n):
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                     B.GBCONV_BF16, B.GBCONV_F32, B.GBCONV_NHWC, B.GBCONV_FLAG_BIAS)
+    B.check(B.gbconv_set_config(B.GBCONV_OP_FWD, prob,
+                                B.gbconv_config_t(block_n, 0, 0, 0, algo)), "set_config")
+    try:
+        r = fwd_case(sh, torch.bfloat16, out_dtype=torch.float32, relu=False, seed=70)
+    finally:
+        B.gbconv_shutdown()
+    assert r["err_i"] <= TOL_ACC32, r["err_i"]
+
+
+@pytest.mark.parametrize("algo", [B.GBCONV_ALGO_IM2COL, B.GBCONV_ALGO_SHIFT])
+def test_fp8_forward_algorithms(algo):
+    sh = ConvShape(2, 256, 12, 12, 128, 3, 3, 1, 1, 1)
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, 1, 1, 1, B.GBCONV_E4M3,
+                     B.GBCONV_BF16, B.GBCONV_NHWC, B.GBCONV_FLAG_BIAS)
+    B.check(B.gbconv_set_config(B.GBCONV_OP_FWD, prob, B.gbconv_config_t(128, 0, 0, 0, algo)),
+            "set_config")
+    try:
+        r = fp8_case(sh, seed=71)
+    finally:
+        B.gbconv_shutdown()
+    assert r["err_i"] <= TOL_BF16_OUT and r["err_ii"] <= TOL_FP8, r

@@ -72,12 +72,22 @@ def test_grouped_small():
 
 
 def test_grouped_matches_single_launches_bitwise():
+    """The grouped launch runs the im2col kernel body; single launches forced
+    onto the same algorithm and tile width reproduce it bit for bit."""
     xs, ws, bs, _ = _inputs(SMALL, 610)
     ys = F.conv2d_grouped(xs, ws, bs, [s.stride for s in SMALL], [s.pad for s in SMALL])
-    for i, sh in enumerate(SMALL):
-        y1 = F.conv2d(xs[i], ws[i], bs[i], sh.stride, sh.pad, 1, False, "NHWC")
-        F.device_error()
-        assert torch.equal(y1, ys[i]), i
+    try:
+        for i, sh in enumerate(SMALL):
+            prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, 1,
+                             B.GBCONV_BF16, B.GBCONV_BF16, B.GBCONV_NHWC, B.GBCONV_FLAG_BIAS)
+            s, cfg = B.gbconv_get_config(B.GBCONV_OP_FWD, prob)
+            cfg.algo = B.GBCONV_ALGO_IM2COL
+            B.check(B.gbconv_set_config(B.GBCONV_OP_FWD, prob, cfg), "set_config")
+            y1 = F.conv2d(xs[i], ws[i], bs[i], sh.stride, sh.pad, 1, False, "NHWC")
+            F.device_error()
+            assert torch.equal(y1, ys[i]), i
+    finally:
+        B.gbconv_shutdown()
 
 
 def test_grouped_workload_64_problems_graph():
