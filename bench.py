@@ -293,6 +293,13 @@ def run_ours(args, rank, world, local):
     flops_step = sum(l.sh.flops for l in layers)
     value = flops_step * args.steps * world / (res["ms_total"] * 1e-3) / 1e12
     per_layer = resnet_report(layers, res, pk, 2)
+    # Each layer alone, K launches back to back in one graph (programmatic
+    # launch overlapping consecutive launches): the per-layer cost inside the
+    # headline step.
+    for lay, row in zip(layers, per_layer):
+        r1 = bench_layers([lay], max(3, min(args.steps, 50)), 1, nsets, torch, dist_on)
+        row["us_overlapped"] = round(r1["ms_per_step"] * 1e3, 2)
+        row["tflops_overlapped"] = round(lay.sh.flops / (r1["ms_per_step"] * 1e-3) / 1e12, 1)
     # dominant kernel: the launch with the largest time share
     j = max(range(len(layers)), key=lambda i: res["launch_us"][i])
     dom = per_layer[j]

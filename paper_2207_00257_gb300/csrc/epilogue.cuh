@@ -10,6 +10,20 @@
 
 namespace gbc {
 
+// Epilogue shape per tile width: 256-column tiles carry the most output per
+// MMA, so they get 16 epilogue warps (four per TMEM lane quarter) to hide the
+// per-chunk latency chain; narrower tiles get 8. Either way the warps share 64
+// KB of staging: NBUF 2 KB BF16 chunk buffers per warp (NBUF-1 TMA stores may
+// still be reading while one is filled), or NBUF/2 4 KB FP32 ones.
+constexpr int EPI_TOTAL_BYTES = 65536;
+template <int BN>
+struct EpiShape {
+    static constexpr int warps = BN >= 256 ? 16 : 8;
+    static constexpr int threads = 64 + 32 * warps;  // + producer and MMA warps
+    static constexpr int warp_bytes = EPI_TOTAL_BYTES / warps;
+    static constexpr int nbuf = warp_bytes / 2048;   // 2 or 4
+};
+
 // What the epilogue needs to know about the output.
 struct EpiArgs {
     int K;                 // output channels (columns >= K are never stored)
@@ -37,9 +51,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // at coordinates (col0, c1) of a 2-D map, or (col0, c1, c2) of a 3-D map when
 // c2 >= 0.
 //   BF16 output: 32 rows x 64 B, 64-byte swizzle (16-B unit c of row r sits at
-//                unit c ^ ((r >> 1) & 3)), two 2 KB halves used alternately;
-//   FP32 output: 32 rows x 128 B, 128-byte swizzle (unit c ^ (r & 7)).
-template <bool FP8>
+//                unit c ^ ((r >> 1) & 3)), NBUF 2 KB buffers used in turn;
+//   FP32 output: 32 rows x 128 B, 128-byte swizzle (unit c ^ (r & 7)), NBUF/2
+//                4 KB buffers used in turn.
+template <bool FP8, int NBUF>
 __device__ __forceinline__ void epilogue_chunk(const uint32_t (&v)[32], const EpiArgs &pa,
                                                const CUtensorMap *tmY, float xs, int col0,
                                                int c1, int c2, int lane, uint8_t *sbuf, int &ebuf) {
@@ -59,9 +74,10 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&v)[32], const Ep
         f[i] = a;
     }
     if (pa.out_f32) {
-        if (lane == 0) ptx::bulk_wait_read<0>();
+        uint8_t *b = sbuf + (ebuf % (NBUF / 2)) * 4096;
+        if (lane == 0) ptx::bulk_wait_read<NBUF / 2 - 1>();
         __syncwarp();
-        uint8_t *dst = sbuf + lane * 128;
+        uint8_t *dst = b + lane * 128;
 #pragma unroll
         for (int c = 0; c < 8; ++c)
             *reinterpret_cast<uint4 *>(dst + ((c ^ (lane & 7)) << 4)) =
@@ -70,12 +86,13 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&v)[32], const Ep
         ptx::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-            store_chunk(tmY, sbuf, col0, c1, c2);
+            store_chunk(tmY, b, col0, c1, c2);
             ptx::bulk_commit();
         }
+        ebuf = (ebuf + 1) % (NBUF / 2);
     } else {
         uint8_t *b = sbuf + ebuf * 2048;
-        if (lane == 0) ptx::bulk_wait_read<1>();
+        if (lane == 0) ptx::bulk_wait_read<NBUF - 1>();
         __syncwarp();
         uint8_t *dst = b + lane * 64;
 #pragma unroll
@@ -90,7 +107,7 @@ __device__ __forceinline__ void epilogue_chunk(const uint32_t (&v)[32], const Ep
             store_chunk(tmY, b, col0, c1, c2);
             ptx::bulk_commit();
         }
-        ebuf ^= 1;
+        ebuf = (ebuf + 1) % NBUF;
     }
 }
 

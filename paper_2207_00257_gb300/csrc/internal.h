@@ -69,6 +69,7 @@ gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg, const void *x,
                               void *y, cudaStream_t st);
 // tc_fwd_shift.cu: stride-1 layers, one input band per channel block.
 bool tc_fwd_shift_supported(const Dims &d, int block_n);
+bool tc_fwd_shift_preferred(const Dims &d, int block_n);  // automatic choice
 gbconv_status_t launch_tc_fwd_shift(const Dims &d, const TcConfig &cfg, const void *x,
                                     const void *w, const float *bias, const float *x_scale,
                                     const float *w_scale, void *y, cudaStream_t st);

@@ -44,10 +44,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int A_BYTES = BM * 128;  // 128 pixels x 128 bytes of channels
-constexpr int NTHREADS = 320;
-constexpr int EPI_WARPS = 8;
-constexpr int EPI_BYTES = 4096;    // staging buffer per epilogue warp
-constexpr int EPI_TOTAL = EPI_WARPS * EPI_BYTES;
+constexpr int EPI_TOTAL = EPI_TOTAL_BYTES;
 constexpr int SMEM_ALIGN = 1024;
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -108,7 +105,10 @@ __device__ __forceinline__ void decode(const FwdParams<G> &prm, int tile, int &g
 }
 
 template <int BN, bool FP8, int G>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_constant__ FwdParams<G> prm) {
+__global__ void __launch_bounds__(EpiShape<BN>::threads, 1) tc_fwd_kernel(const __grid_constant__ FwdParams<G> prm) {
+    constexpr int EPI_WARPS = EpiShape<BN>::warps;
+    constexpr int EPI_BYTES = EpiShape<BN>::warp_bytes;
+    constexpr int EPI_GROUPS = EPI_WARPS / 4;  // warps per TMEM lane quarter
     constexpr int KE = FP8 ? 128 : 64;         // reduction elements per 128-byte row
     constexpr int KSTEPS = 4;                  // 4 MMAs of 32 bytes of K per row
     constexpr int TCOLS = TmemCols<BN>::v;
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_consta
         // ------------------------------ epilogue ------------------------------
         const int ew = warp - 2;        // 0..7
         const int quarter = warp & 3;   // TMEM lanes this warp may access
-        const int half = ew >> 2;       // this warp takes chunks j with j % 2 == half
+        const int half = ew >> 2;       // this warp takes chunks j with j % EPI_GROUPS == half
         uint8_t *sbuf = sEpi + ew * EPI_BYTES;
         int ebuf = 0;
         int local = 0;
@@ -305,13 +305,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_consta
             const float xs = FP8 ? __ldg(pa.x_scale) : 1.f;
             const int nchunks = pa.bn / 32;
             bool released = false;
-            for (int j = half; j < nchunks; j += 2) {
+            for (int j = half; j < nchunks; j += EPI_GROUPS) {
                 uint32_t v[32];
                 ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
                                             (uint32_t)(acc * BN + j * 32),
                                         v);
                 ptx::tmem_ld_wait();
-                if (j + 2 >= nchunks) {  // last TMEM read of this warp for this tile
+                if (j + EPI_GROUPS >= nchunks) {  // last TMEM read of this warp for this tile
                     ptx::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_kernel(const __grid_consta
                 }
                 const int col0 = nt * pa.bn + j * 32;
                 if (col0 >= pa.K || row0 >= pa.M) continue;  // chunk entirely outside y
-                epilogue_chunk<FP8>(v, EpiArgs{pa.K, pa.relu, pa.out_f32, pa.bias, pa.w_scale},
+                epilogue_chunk<FP8, EpiShape<BN>::nbuf>(v, EpiArgs{pa.K, pa.relu, pa.out_f32, pa.bias, pa.w_scale},
                                     &prm.tmY[g], xs, col0, row0, -1, lane, sbuf, ebuf);
             }
             if (!released) {
@@ -365,7 +365,7 @@ gbconv_status_t launch_kernel(const FwdParams<G> &prm, int grid, cudaStream_t st
     });
     if (attr_err != cudaSuccess) return cuda_status(attr_err);
     size_t smem = smem_bytes(BN, prm.stages);
-    return cuda_status(launch_pdl(tc_fwd_kernel<BN, FP8, G>, dim3(grid), dim3(NTHREADS), smem, st, prm));
+    return cuda_status(launch_pdl(tc_fwd_kernel<BN, FP8, G>, dim3(grid), dim3(EpiShape<BN>::threads), smem, st, prm));
 }
 
 // Fills pa, tmA, tmB for one problem; bn is the tile width used.
@@ -478,11 +478,11 @@ gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void 
     if (cfg.block_n != 32 && cfg.block_n != 64 && cfg.block_n != 128 && cfg.block_n != 256)
         return GBCONV_ERR_INVALID_ARG;
     // Automatic choice: the shifted-band kernel for stride-1 layers with more
-    // than one filter tap (a 1x1 layer gains nothing from it and would compute
-    // the extended rows' spare columns).
-    const bool want_shift = cfg.algo == GBCONV_ALGO_SHIFT ||
-                            (cfg.algo == GBCONV_ALGO_AUTO && d.R * d.S > 1);
-    if (want_shift && tc_fwd_shift_supported(d, cfg.block_n))
+    // than one filter tap whose filter fits in shared memory (a 1x1 layer
+    // gains nothing from it and would compute the extended rows' spare columns).
+    if (cfg.algo == GBCONV_ALGO_SHIFT && tc_fwd_shift_supported(d, cfg.block_n))
+        return launch_tc_fwd_shift(d, cfg, x, w, bias, x_scale, w_scale, y, st);
+    if (cfg.algo == GBCONV_ALGO_AUTO && d.R * d.S > 1 && tc_fwd_shift_preferred(d, cfg.block_n))
         return launch_tc_fwd_shift(d, cfg, x, w, bias, x_scale, w_scale, y, st);
     if (cfg.algo == GBCONV_ALGO_SHIFT) return GBCONV_ERR_UNSUPPORTED;
     if (cfg.stages < 2 || cfg.stages > max_stages(cfg.block_n)) cfg.stages = max_stages(cfg.block_n);

@@ -41,10 +41,7 @@
 namespace gbc {
 namespace {
 
-constexpr int NTHREADS = 320;
-constexpr int EPI_WARPS = 8;
-constexpr int EPI_BYTES = 4096;
-constexpr int EPI_TOTAL = EPI_WARPS * EPI_BYTES;
+constexpr int EPI_TOTAL = EPI_TOTAL_BYTES;
 constexpr int SMEM_ALIGN = 1024;
 constexpr int BAR_BYTES = 512;
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -80,8 +77,11 @@ __device__ __forceinline__ void sdecode(const ShiftParams &p, int tile, int &n, 
 }
 
 template <int BN, bool FP8>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(EpiShape<BN>::threads, 1)
     tc_fwd_shift_kernel(const __grid_constant__ ShiftParams prm) {
+    constexpr int EPI_WARPS = EpiShape<BN>::warps;
+    constexpr int EPI_BYTES = EpiShape<BN>::warp_bytes;
+    constexpr int EPI_GROUPS = EPI_WARPS / 4;  // warps per TMEM lane quarter
     constexpr int KE = FP8 ? 128 : 64;
     constexpr int TCOLS = (2 * BN < 32) ? 32 : 2 * BN;
     constexpr int B_TILE = BN * 128;
@@ -334,13 +334,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const float xs = FP8 ? __ldg(prm.x_scale) : 1.f;
             const int nchunks = prm.bn / 32;
             bool released = false;
-            for (int j = half; j < nchunks; j += 2) {
+            for (int j = half; j < nchunks; j += EPI_GROUPS) {
                 uint32_t v[32];
                 ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
                                             (uint32_t)(acc * BN + j * 32),
                                         v);
                 ptx::tmem_ld_wait();
-                if (j + 2 >= nchunks) {
+                if (j + EPI_GROUPS >= nchunks) {
                     ptx::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 const int col0 = nt * prm.bn + j * 32;
                 if (!rows_ok || col0 >= prm.epi.K) continue;
-                epilogue_chunk<FP8>(v, prm.epi, &prm.tmY, xs, col0, q0, n * prm.P + p, lane, sbuf,
+                epilogue_chunk<FP8, EpiShape<BN>::nbuf>(v, prm.epi, &prm.tmY, xs, col0, q0, n * prm.P + p, lane, sbuf,
                                     ebuf);
             }
             if (!released) {
@@ -433,7 +433,7 @@ gbconv_status_t launch(const ShiftParams &prm, size_t smem, int grid, cudaStream
     });
     if (attr_err != cudaSuccess) return cuda_status(attr_err);
     return cuda_status(
-        launch_pdl(tc_fwd_shift_kernel<BN, FP8>, dim3(grid), dim3(NTHREADS), smem, st, prm));
+        launch_pdl(tc_fwd_shift_kernel<BN, FP8>, dim3(grid), dim3(EpiShape<BN>::threads), smem, st, prm));
 }
 
 }  // namespace
@@ -441,6 +441,14 @@ gbconv_status_t launch(const ShiftParams &prm, size_t smem, int grid, cudaStream
 bool tc_fwd_shift_supported(const Dims &d, int block_n) {
     Plan p;
     return tc_fwd_supported(d) && make_plan(d, block_n, &p);
+}
+
+bool tc_fwd_shift_preferred(const Dims &d, int block_n) {
+    // Measured on GB300: the band kernel wins when the whole filter stays in
+    // shared memory; when the filter streams, the im2col kernel's deeper
+    // combined ring is faster.
+    Plan p;
+    return tc_fwd_supported(d) && make_plan(d, block_n, &p) && p.b_resident;
 }
 
 gbconv_status_t launch_tc_fwd_shift(const Dims &d, const TcConfig &cfg, const void *x,
