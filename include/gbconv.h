@@ -89,12 +89,15 @@ typedef struct {
  * shared-memory pipeline depth; split_k: number of slices the reduction is
  * cut into (wgrad); raster: 0 = output-channel tiles fastest, 1 = pixel tiles
  * fastest; algo (tensor-core forward and data gradient): GBCONV_ALGO_AUTO,
- * GBCONV_ALGO_IM2COL (one TMA im2col tile per filter tap) or
+ * GBCONV_ALGO_IM2COL (one TMA im2col tile per filter tap),
  * GBCONV_ALGO_SHIFT (stride 1 only: one input band per channel block, filter
- * taps as row shifts of it). A zero field means "library default". */
+ * taps as row shifts of it) or GBCONV_ALGO_SHIFT_T (the same band with the
+ * GEMM transposed: output channels on the MMA's M, 256 positions on N; stride
+ * 1 and K <= 128 only). A zero field means "library default". */
 #define GBCONV_ALGO_AUTO 0
 #define GBCONV_ALGO_IM2COL 1
 #define GBCONV_ALGO_SHIFT 2
+#define GBCONV_ALGO_SHIFT_T 3
 typedef struct {
     int32_t block_n;
     int32_t stages;

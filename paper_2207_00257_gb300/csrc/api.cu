@@ -412,7 +412,7 @@ gbconv_status_t gbconv_set_config(int32_t op, const gbconv_problem_t *prob,
         cfg->block_n != 256)
         return GBCONV_ERR_INVALID_ARG;
     if (cfg->split_k < 0 || cfg->split_k > 1024 || cfg->stages < 0 || cfg->raster < 0 ||
-        cfg->raster > 1 || cfg->algo < GBCONV_ALGO_AUTO || cfg->algo > GBCONV_ALGO_SHIFT)
+        cfg->raster > 1 || cfg->algo < GBCONV_ALGO_AUTO || cfg->algo > GBCONV_ALGO_SHIFT_T)
         return GBCONV_ERR_INVALID_ARG;
     TcConfig c = config_for(op, *prob, d);  // defaults for zero fields
     if (cfg->block_n) c.block_n = cfg->block_n;
@@ -450,8 +450,10 @@ gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void
         if (tc) {
             for (int bn : {32, 64, 128, 256}) {
                 if (bn > 32 && bn / 2 >= kout) continue;  // wider than needed
-                for (int algo : {GBCONV_ALGO_IM2COL, GBCONV_ALGO_SHIFT}) {
+                for (int algo : {GBCONV_ALGO_IM2COL, GBCONV_ALGO_SHIFT, GBCONV_ALGO_SHIFT_T}) {
                     if (algo == GBCONV_ALGO_SHIFT && !tc_fwd_shift_supported(t, bn)) continue;
+                    // the transposed kernel picks its own tile: try it once
+                    if (algo == GBCONV_ALGO_SHIFT_T && (!tc_fwd_t_tile(t) || bn != 64)) continue;
                     for (int raster : {0, 1}) {
                         TcConfig c = base;
                         c.block_n = bn;

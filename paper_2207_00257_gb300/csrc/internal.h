@@ -73,6 +73,11 @@ bool tc_fwd_shift_preferred(const Dims &d, int block_n);  // automatic choice
 gbconv_status_t launch_tc_fwd_shift(const Dims &d, const TcConfig &cfg, const void *x,
                                     const void *w, const float *bias, const float *x_scale,
                                     const float *w_scale, void *y, cudaStream_t st);
+// tc_fwd_t.cu: stride-1 band kernel with output channels on the MMA's M.
+int tc_fwd_t_tile(const Dims &d);  // output-channel tile (64 / 128), 0 if unsuitable
+gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, const float *bias,
+                                const float *x_scale, const float *w_scale, void *y,
+                                cudaStream_t st);
 gbconv_status_t launch_tc_grouped(int count, const Dims *d, const TcConfig *cfg,
                                   const void *const *x, const void *const *w,
                                   const float *const *bias, void *const *y, cudaStream_t st);

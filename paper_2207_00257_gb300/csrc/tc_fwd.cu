@@ -480,11 +480,16 @@ gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void 
     // Automatic choice: the shifted-band kernel for stride-1 layers with more
     // than one filter tap whose filter fits in shared memory (a 1x1 layer
     // gains nothing from it and would compute the extended rows' spare columns).
+    if (cfg.algo == GBCONV_ALGO_SHIFT_T || (cfg.algo == GBCONV_ALGO_AUTO && d.R * d.S > 1)) {
+        if (tc_fwd_t_tile(d))
+            return launch_tc_fwd_t(d, x, w, bias, x_scale, w_scale, y, st);
+        if (cfg.algo == GBCONV_ALGO_SHIFT_T) return GBCONV_ERR_UNSUPPORTED;
+    }
     if (cfg.algo == GBCONV_ALGO_SHIFT && tc_fwd_shift_supported(d, cfg.block_n))
         return launch_tc_fwd_shift(d, cfg, x, w, bias, x_scale, w_scale, y, st);
     if (cfg.algo == GBCONV_ALGO_AUTO && d.R * d.S > 1 && tc_fwd_shift_preferred(d, cfg.block_n))
         return launch_tc_fwd_shift(d, cfg, x, w, bias, x_scale, w_scale, y, st);
-    if (cfg.algo == GBCONV_ALGO_SHIFT) return GBCONV_ERR_UNSUPPORTED;
+    if (cfg.algo == GBCONV_ALGO_SHIFT) return GBCONV_ERR_UNSUPPORTED;  // not a stride-1 band layer
     if (cfg.stages < 2 || cfg.stages > max_stages(cfg.block_n)) cfg.stages = max_stages(cfg.block_n);
     if (d.M() == 0) return GBCONV_OK;
     FwdParams<1> prm;

@@ -1,0 +1,568 @@
+// tc_fwd_t.cu -- "transposed" shifted-band forward convolution for stride-1
+// layers with at most 128 output channels.
+//
+// Same operation and input band as tc_fwd_shift.cu (one padded input band per
+// channel block, every filter tap a row shift of it; forward pass of a
+// convolutional layer, paper Sec. 5.B), but the GEMM is computed transposed:
+//
+//   D^T[k][e] = sum_{(r,s), c} W[k][(r,s)][c] * band[e + r*dh*Wx + s*dw][c]
+//
+// with M = KT output channels (64 or 128) and N = 256 extended output
+// positions per tcgen05.mma. On GB300 one MMA instruction costs about the
+// same for N = 64 and N = 128 and only grows from N = 128 to 256, so a layer
+// with 64 or 128 output channels runs 1.6-1.8x more tensor work per
+// instruction this way than with pixels on M.
+//
+//  * Tile: 256 consecutive extended positions = TR = 256 / Wx output rows of
+//    one image, times KT output channels.
+//  * A operand: filter tile W[(r,s), c block] = KT rows of 128 bytes, resident
+//    in shared memory when the whole filter fits, otherwise streamed.
+//  * B operand: 256 band rows starting at the tap's shift (K-major, 128-byte
+//    swizzle; any 128-byte row is a valid start).
+//  * TMEM: two 256-column accumulators. For M = 128 row k of D^T sits in lane
+//    k; for M = 64 row k sits in lane 32*(k/16) + k%16 (lanes 16-31 of each
+//    quarter unused).
+//  * Epilogue: 8 warps, two groups of four (one warp per TMEM lane quarter).
+//    Group g takes 32-position chunks j = g, g+2, ... Each thread holds one
+//    output channel k (bias and FP8 scale are per-thread constants) and 32
+//    positions; pairs of lanes exchange values so that each writes 32-bit
+//    words of two adjacent channels into a [32 positions][KT channels] BF16
+//    (or FP32) tile in shared memory (128-byte swizzled rows). A named barrier
+//    joins the group, then one thread stores the tile with TMA through a 3-D
+//    map of y as [N*P][Q][K] (positions q >= Q and channels >= K clipped).
+//
+// Warp roles and bounded waits as in tc_fwd.cu (320 threads).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "internal.h"
+#include "launch.cuh"
+#include "ptx.cuh"
+
+namespace gbc {
+namespace {
+
+constexpr int NPOS = 256;  // positions per tile (MMA N)
+constexpr int NTHREADS = 320;
+constexpr int EPI_WARPS = 8;
+constexpr int SMEM_ALIGN = 1024;
+constexpr int BAR_BYTES = 512;
+constexpr int SMEM_LIMIT = 227 * 1024;
+constexpr int MAX_SA = 4, MAX_SB = 12;
+
+struct TParams {
+    CUtensorMap tmX;  // x [N][H][W][C], box {KE, Wx, nr, 1}
+    CUtensorMap tmW;  // w [K][R*S][C], box {KE, 1, KT}
+    CUtensorMap tmY;  // y [N*P][Q][K], box {64 (BF16) | 32 (FP32), 32, 1}
+    int N, P, Q, K;
+    int pw, ph, dh, dw, S, RS;
+    int wx_log2, TR;
+    int c_blocks, k_tiles, p_tiles, num_tiles;
+    int band_bytes, band_stride, w_resident, stages_a, stages_b;
+    int relu, out_f32;
+    const float *bias, *x_scale, *w_scale;
+    Guard guard;
+};
+
+__device__ __forceinline__ void tdecode(const TParams &p, int tile, int &n, int &p0, int &kt) {
+    kt = tile % p.k_tiles;
+    const int mt = tile / p.k_tiles;
+    n = mt / p.p_tiles;
+    p0 = (mt - n * p.p_tiles) * p.TR;
+}
+
+__device__ __forceinline__ void named_bar(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+template <int KT, bool FP8>
+__global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_constant__ TParams prm) {
+    constexpr int KE = FP8 ? 128 : 64;
+    constexpr int TCOLS = 2 * NPOS;          // two 256-column accumulators
+    constexpr int W_TILE = KT * 128;         // one filter tile (tap, channel block)
+    constexpr int STAGE_T = 32 * KT * 4;     // staging tile, worst case FP32: 32 x KT x 4 B
+    constexpr int EPI_TOTAL = 2 * 2 * STAGE_T;  // two groups x two buffers
+    constexpr int KPW = KT / 4;              // output channels per warp (16 or 32)
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + SMEM_ALIGN - 1) & ~uintptr_t(SMEM_ALIGN - 1));
+    const int SA = prm.stages_a, SB = prm.stages_b;
+    const int w_slots = prm.w_resident ? prm.RS * prm.c_blocks : SB;
+    uint8_t *sA = base;                              // band ring
+    uint8_t *sW = sA + SA * prm.band_stride;         // filter tiles
+    uint8_t *sEpi = sW + w_slots * W_TILE;           // staging
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sEpi + EPI_TOTAL);
+    uint64_t *fullA = bars;
+    uint64_t *emptyA = fullA + MAX_SA;
+    uint64_t *fullW = emptyA + MAX_SA;
+    uint64_t *emptyW = fullW + MAX_SB;
+    uint64_t *tfull = emptyW + MAX_SB;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *done = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t lim = prm.guard.wait_ns;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < SA; ++i) {
+            ptx::mbar_init(&fullA[i], 1);
+            ptx::mbar_init(&emptyA[i], 1);
+        }
+        for (int i = 0; i < (prm.w_resident ? 1 : SB); ++i) {
+            ptx::mbar_init(&fullW[i], 1);
+            ptx::mbar_init(&emptyW[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&tfull[i], 1);
+            ptx::mbar_init(&tempty[i], EPI_WARPS);
+        }
+        ptx::mbar_init(done, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(tmem_slot, TCOLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
+
+    auto fail = [&]() {
+        *abort_flag = 1;
+        atomicOr(prm.guard.err, DEVERR_TIMEOUT);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------ producer ------------------------------
+            const bool skip = prm.guard.skip_loads != 0;
+            bool ok = true;
+            int issued_w = 0;
+            if (prm.w_resident && !skip) {
+                // resident filter: every (channel block, tap) tile of output-channel tile 0
+                // (a resident filter implies a single output-channel tile)
+                ptx::mbar_arrive_expect_tx(&fullW[0], (uint32_t)(prm.RS * prm.c_blocks * W_TILE));
+                for (int cb = 0; cb < prm.c_blocks; ++cb)
+                    for (int t = 0; t < prm.RS; ++t)
+                        ptx::tma_load_3d(sW + (cb * prm.RS + t) * W_TILE, &prm.tmW, &fullW[0],
+                                         cb * KE, t, 0);
+                issued_w = 1;
+            }
+            int sa = 0, sb = 0;
+            uint32_t pa = 0, pb = 0;
+            int issued_a = 0, issued_b = 0;
+            for (int tile = blockIdx.x; ok && tile < prm.num_tiles; tile += gridDim.x) {
+                int n, p0, kt;
+                tdecode(prm, tile, n, p0, kt);
+                for (int cb = 0; ok && cb < prm.c_blocks; ++cb) {
+                    if (!ptx::mbar_wait(&emptyA[sa], pa ^ 1, lim, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    if (!skip) {
+                        ptx::mbar_arrive_expect_tx(&fullA[sa], (uint32_t)prm.band_bytes);
+                        ptx::tma_load_4d(sA + sa * prm.band_stride, &prm.tmX, &fullA[sa], cb * KE,
+                                         -prm.pw, p0 - prm.ph, n);
+                        ++issued_a;
+                    }
+                    if (++sa == SA) {
+                        sa = 0;
+                        pa ^= 1;
+                    }
+                    if (prm.w_resident) continue;
+                    for (int t = 0; t < prm.RS; ++t) {
+                        if (!ptx::mbar_wait(&emptyW[sb], pb ^ 1, lim, abort_flag)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        if (!skip) {
+                            ptx::mbar_arrive_expect_tx(&fullW[sb], (uint32_t)W_TILE);
+                            ptx::tma_load_3d(sW + sb * W_TILE, &prm.tmW, &fullW[sb], cb * KE, t,
+                                             kt * KT);
+                            ++issued_b;
+                        }
+                        if (++sb == SB) {
+                            sb = 0;
+                            pb ^= 1;
+                        }
+                    }
+                }
+            }
+            volatile int zero = 0;
+            {
+                int st = sa;
+                uint32_t ph = pa;
+                for (int i = 0; i < min(issued_a, SA); ++i) {
+                    if (st == 0) {
+                        st = SA;
+                        ph ^= 1;
+                    }
+                    --st;
+                    if (!ptx::mbar_wait(&fullA[st], ph, lim, &zero)) fail();
+                }
+            }
+            {
+                int st = sb;
+                uint32_t ph = pb;
+                for (int i = 0; i < min(issued_b, SB); ++i) {
+                    if (st == 0) {
+                        st = SB;
+                        ph ^= 1;
+                    }
+                    --st;
+                    if (!ptx::mbar_wait(&fullW[st], ph, lim, &zero)) fail();
+                }
+            }
+            if (issued_w && !ptx::mbar_wait(&fullW[0], 0, lim, &zero)) fail();
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------ MMA issuer ----------------------------
+            bool ok = true;
+            if (prm.w_resident && !ptx::mbar_wait(&fullW[0], 0, lim, abort_flag)) {
+                fail();
+                ok = false;
+            }
+            uint32_t idesc = FP8 ? ptx::idesc_e4m3(NPOS) : ptx::idesc_bf16(NPOS);
+            idesc = (idesc & ~(0x1Fu << 24)) | ((uint32_t)(KT >> 4) << 24);  // M = KT
+            int sa = 0, sb = 0;
+            uint32_t pa = 0, pb = 0;
+            int local = 0;
+            for (int tile = blockIdx.x; ok && tile < prm.num_tiles; tile += gridDim.x, ++local) {
+                const int acc = local & 1;
+                const uint32_t aph = (local >> 1) & 1;
+                if (!ptx::mbar_wait(&tempty[acc], aph ^ 1, lim, abort_flag)) {
+                    fail();
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(acc * NPOS);
+                for (int cb = 0; ok && cb < prm.c_blocks; ++cb) {
+                    if (!ptx::mbar_wait(&fullA[sa], pa, lim, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t band = ptx::smem_addr(sA + sa * prm.band_stride);
+                    int r = 0, s = 0;
+                    for (int t = 0; t < prm.RS; ++t) {
+                        uint32_t w_addr;
+                        if (prm.w_resident) {
+                            w_addr = ptx::smem_addr(sW + (cb * prm.RS + t) * W_TILE);
+                        } else {
+                            if (!ptx::mbar_wait(&fullW[sb], pb, lim, abort_flag)) {
+                                fail();
+                                ok = false;
+                                break;
+                            }
+                            ptx::tc_fence_after();
+                            w_addr = ptx::smem_addr(sW + sb * W_TILE);
+                        }
+                        const uint32_t shift = (uint32_t)(((r * prm.dh) << prm.wx_log2) + s * prm.dw);
+                        const uint64_t ad = ptx::sdesc_kmajor_sw128(w_addr);
+                        const uint64_t bd = ptx::sdesc_kmajor_sw128(band + shift * 128u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint32_t accum = (cb | t | k) != 0;
+                            if (FP8)
+                                ptx::mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                            else
+                                ptx::mma_f16(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                        }
+                        if (!prm.w_resident) {
+                            ptx::mma_commit(&emptyW[sb]);
+                            if (++sb == SB) {
+                                sb = 0;
+                                pb ^= 1;
+                            }
+                        }
+                        if (++s == prm.S) {
+                            s = 0;
+                            ++r;
+                        }
+                    }
+                    if (!ok) break;
+                    ptx::mma_commit(&emptyA[sa]);
+                    if (++sa == SA) {
+                        sa = 0;
+                        pa ^= 1;
+                    }
+                }
+                if (!ok) break;
+                ptx::mma_commit(&tfull[acc]);
+            }
+            ptx::mma_commit(done);
+            volatile int zero = 0;
+            if (!ptx::mbar_wait(done, 0, lim, &zero)) fail();
+        }
+    } else {
+        // ------------------------------ epilogue ------------------------------
+        const int ew = warp - 2;            // 0..7
+        const int quarter = warp & 3;       // TMEM lane quarter
+        const int group = ew >> 2;          // chunks j with j % 2 == group
+        // this thread's output-channel row within the tile (valid lanes only)
+        const bool lane_ok = KT == 128 || lane < 16;
+        const int krow = quarter * KPW + (KT == 128 ? lane : (lane & 15));
+        uint8_t *gbuf = sEpi + group * 2 * STAGE_T;
+        int ebuf = 0;
+        const int wx_mask = (1 << prm.wx_log2) - 1;
+        const float xs = FP8 ? __ldg(prm.x_scale) : 1.f;
+        int local = 0;
+        for (int tile = blockIdx.x; tile < prm.num_tiles; tile += gridDim.x, ++local) {
+            int n, p0, kt;
+            tdecode(prm, tile, n, p0, kt);
+            const int acc = local & 1;
+            const uint32_t aph = (local >> 1) & 1;
+            if (!ptx::mbar_wait(&tfull[acc], aph, lim, abort_flag)) {
+                fail();
+                break;
+            }
+            ptx::tc_fence_after();
+            const int k = kt * KT + krow;
+            float scl = 1.f, bia = 0.f;
+            if (lane_ok && k < prm.K) {
+                if (FP8) scl = xs * __ldg(prm.w_scale + k);
+                if (prm.bias) bia = __ldg(prm.bias + k);
+            }
+            for (int j = group; j < NPOS / 32; j += 2) {
+                uint32_t v[32];
+                ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                                            (uint32_t)(acc * NPOS + j * 32),
+                                        v);
+                ptx::tmem_ld_wait();
+                if (j + 2 >= NPOS / 32) {
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+                }
+                // chunk j = positions 32j .. 32j+31 = output row p, columns q0..q0+31
+                const int p = p0 + ((32 * j) >> prm.wx_log2);
+                const int q0 = (32 * j) & wx_mask;
+                const bool store = p < prm.P && q0 < prm.Q;  // warp-uniform
+                float f[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    float a = __uint_as_float(v[i]);
+                    if (FP8) a = a * scl;
+                    a = a + bia;
+                    if (prm.relu) a = fmaxf(a, 0.f);
+                    f[i] = a;
+                }
+                uint8_t *buf = gbuf + ebuf * STAGE_T;
+                if (store) {
+                    // staging tile [32 positions][KT channels]: 64-channel halves of
+                    // 128-byte rows (BF16) or 32-channel quarters (FP32), each
+                    // 32 rows x 128 B with the 128-byte swizzle (unit u ^ (row & 7))
+                    if (threadIdx.x == 64 + group * 128) ptx::bulk_wait_read<1>();
+                    named_bar(1 + group, 128);
+                    if (!prm.out_f32) {
+                        // lanes 2i / 2i+1 hold channels k, k+1: exchange so that the
+                        // even lane writes (k, k+1) of even positions, the odd lane of odd ones
+#pragma unroll
+                        for (int i = 0; i < 32; i += 2) {
+                            const float o0 = __shfl_xor_sync(0xffffffffu, f[i], 1);
+                            const float o1 = __shfl_xor_sync(0xffffffffu, f[i + 1], 1);
+                            const bool odd = lane & 1;
+                            const int e = odd ? i + 1 : i;
+                            const uint32_t word = odd ? pack2(o1, f[i + 1]) : pack2(f[i], o0);
+                            const int kc = krow & ~1;              // even channel of the pair
+                            const int half = kc >> 6, kb = (kc & 63) * 2;
+                            uint8_t *row = buf + half * 4096 + e * 128;
+                            if (lane_ok)
+                                *reinterpret_cast<uint32_t *>(
+                                    row + ((((kb >> 4) ^ (e & 7)) << 4) | (kb & 15))) = word;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            const int qd = krow >> 5, kb = (krow & 31) * 4;
+                            uint8_t *row = buf + qd * 4096 + e * 128;
+                            if (lane_ok)
+                                *reinterpret_cast<float *>(
+                                    row + ((((kb >> 4) ^ (e & 7)) << 4) | (kb & 15))) = f[e];
+                        }
+                    }
+                    ptx::fence_proxy_async_smem();
+                    named_bar(1 + group, 128);
+                    if (threadIdx.x == 64 + group * 128) {
+                        const int cols = prm.out_f32 ? 32 : 64;
+                        for (int h = 0; h < KT / cols; ++h) {
+                            const int kc = kt * KT + h * cols;
+                            if (kc < prm.K)
+                                ptx::tma_store_3d(&prm.tmY, buf + h * 4096, kc, q0, n * prm.P + p);
+                        }
+                        ptx::bulk_commit();
+                    }
+                    ebuf ^= 1;
+                }
+            }
+        }
+        if (threadIdx.x == 64 + group * 128) ptx::bulk_wait<0>();
+    }
+
+    __syncwarp();
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == 1) ptx::tmem_dealloc(tmem_base, TCOLS);
+}
+
+struct TPlan {
+    int wx_log2, TR, nr, band_bytes, band_stride, c_blocks, w_resident, stages_a, stages_b;
+};
+
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+template <int KT>
+constexpr int epi_total() { return 2 * 2 * 32 * KT * 4; }
+
+bool make_plan(const Dims &d, int kt, TPlan *pl) {
+    if (d.u != 1 || d.v != 1) return false;
+    const bool fp8 = d.in_dtype == GBCONV_E4M3;
+    const int ke = fp8 ? 128 : 64;
+    const int need = d.Q + (d.S - 1) * d.dw;
+    int wx = 32;
+    while (wx < need) wx *= 2;
+    if (wx > NPOS) return false;
+    TPlan p{};
+    p.wx_log2 = ilog2(wx);
+    p.TR = NPOS / wx;
+    p.nr = p.TR + (d.R - 1) * d.dh;
+    if (p.nr > 256) return false;
+    p.band_bytes = 128 * wx * p.nr;
+    p.band_stride = (p.band_bytes + (d.S - 1) * d.dw * 128 + 1023) / 1024 * 1024;
+    if (p.band_stride > 80 * 1024) return false;
+    p.c_blocks = (d.C + ke - 1) / ke;
+    const int epi = kt == 128 ? epi_total<128>() : epi_total<64>();
+    const int budget = SMEM_LIMIT - SMEM_ALIGN - BAR_BYTES - epi;
+    const int wtile = kt * 128;
+    const long long w_total = (long long)d.R * d.S * p.c_blocks * wtile;
+    const int k_tiles = (d.K + kt - 1) / kt;
+    if (k_tiles == 1 && w_total + 2ll * p.band_stride <= budget) {
+        p.w_resident = 1;
+        p.stages_a = (int)std::min<long long>(MAX_SA, (budget - w_total) / p.band_stride);
+        p.stages_b = 0;
+    } else {
+        p.w_resident = 0;
+        p.stages_a = 2;
+        p.stages_b = std::min(MAX_SB, (budget - 2 * p.band_stride) / wtile);
+        if (p.stages_b < 2) return false;
+    }
+    *pl = p;
+    return true;
+}
+
+template <int KT, bool FP8>
+gbconv_status_t launch(const TParams &prm, size_t smem, int grid, cudaStream_t st) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(tc_fwd_t_kernel<KT, FP8>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+    });
+    if (attr_err != cudaSuccess) return cuda_status(attr_err);
+    return cuda_status(launch_pdl(tc_fwd_t_kernel<KT, FP8>, dim3(grid), dim3(NTHREADS), smem, st, prm));
+}
+
+}  // namespace
+
+// Output-channel tile of the transposed kernel for this layer (0 if none fits).
+int tc_fwd_t_tile(const Dims &d) {
+    if (!tc_fwd_supported(d) || d.K > 128) return 0;
+    const int kt = d.K <= 64 ? 64 : 128;
+    TPlan p;
+    return make_plan(d, kt, &p) ? kt : 0;
+}
+
+gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, const float *bias,
+                                const float *x_scale, const float *w_scale, void *y,
+                                cudaStream_t st) {
+    const int kt = tc_fwd_t_tile(d);
+    if (!kt) return GBCONV_ERR_UNSUPPORTED;
+    TPlan pl;
+    make_plan(d, kt, &pl);
+    if (d.M() == 0) return GBCONV_OK;
+    const bool fp8 = d.in_dtype == GBCONV_E4M3;
+    const int eb = fp8 ? 1 : 2, ke = 128 / eb;
+    const CUtensorMapDataType in_t =
+        fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    TParams prm;
+    memset(&prm, 0, sizeof(prm));
+    uint64_t xd[4] = {(uint64_t)d.C, (uint64_t)d.W, (uint64_t)d.H, (uint64_t)d.N};
+    uint64_t xs[3] = {(uint64_t)d.C * eb, (uint64_t)d.W * d.C * eb, (uint64_t)d.H * d.W * d.C * eb};
+    uint32_t xb[4] = {(uint32_t)ke, (uint32_t)(1 << pl.wx_log2), (uint32_t)pl.nr, 1};
+    gbconv_status_t s = encode_tiled(&prm.tmX, in_t, 4, x, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (s != GBCONV_OK) return s;
+    uint64_t wd[3] = {(uint64_t)d.C, (uint64_t)d.R * d.S, (uint64_t)d.K};
+    uint64_t wstr[2] = {(uint64_t)d.C * eb, (uint64_t)d.R * d.S * d.C * eb};
+    uint32_t wbx[3] = {(uint32_t)ke, 1, (uint32_t)kt};
+    s = encode_tiled(&prm.tmW, in_t, 3, w, wd, wstr, wbx, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (s != GBCONV_OK) return s;
+    const bool of32 = d.out_dtype == GBCONV_F32;
+    uint64_t yd[3] = {(uint64_t)d.K, (uint64_t)d.Q, (uint64_t)d.N * d.P};
+    uint64_t ys[2] = {(uint64_t)d.K * (of32 ? 4 : 2), (uint64_t)d.Q * d.K * (of32 ? 4 : 2)};
+    uint32_t yb[3] = {(uint32_t)(of32 ? 32 : 64), 32, 1};
+    s = encode_tiled(&prm.tmY, of32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                     3, y, yd, ys, yb, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (s != GBCONV_OK) return s;
+    prm.N = d.N;
+    prm.P = d.P;
+    prm.Q = d.Q;
+    prm.K = d.K;
+    prm.pw = d.pw;
+    prm.ph = d.ph;
+    prm.dh = d.dh;
+    prm.dw = d.dw;
+    prm.S = d.S;
+    prm.RS = d.R * d.S;
+    prm.wx_log2 = pl.wx_log2;
+    prm.TR = pl.TR;
+    prm.c_blocks = pl.c_blocks;
+    prm.k_tiles = (d.K + kt - 1) / kt;
+    prm.p_tiles = (d.P + pl.TR - 1) / pl.TR;
+    const long long tiles = (long long)d.N * prm.p_tiles * prm.k_tiles;
+    if (tiles >= (1ll << 31)) return GBCONV_ERR_UNSUPPORTED;
+    prm.num_tiles = (int)tiles;
+    prm.band_bytes = pl.band_bytes;
+    prm.band_stride = pl.band_stride;
+    prm.w_resident = pl.w_resident;
+    prm.stages_a = pl.stages_a;
+    prm.stages_b = pl.stages_b;
+    prm.relu = (d.flags & GBCONV_FLAG_RELU) ? 1 : 0;
+    prm.out_f32 = of32;
+    prm.bias = (d.flags & GBCONV_FLAG_BIAS) ? bias : nullptr;
+    prm.x_scale = x_scale;
+    prm.w_scale = w_scale;
+    prm.guard = make_guard();
+    if (!prm.guard.err) return GBCONV_ERR_CUDA;
+    const int w_slots = pl.w_resident ? d.R * d.S * pl.c_blocks : pl.stages_b;
+    const size_t smem = (size_t)SMEM_ALIGN + (size_t)pl.stages_a * pl.band_stride +
+                        (size_t)w_slots * kt * 128 +
+                        (kt == 128 ? epi_total<128>() : epi_total<64>()) + BAR_BYTES;
+    const int grid = std::min(prm.num_tiles, sm_count());
+    if (kt == 64) return fp8 ? launch<64, true>(prm, smem, grid, st) : launch<64, false>(prm, smem, grid, st);
+    return fp8 ? launch<128, true>(prm, smem, grid, st) : launch<128, false>(prm, smem, grid, st);
+}
+
+}  // namespace gbc

@@ -258,7 +258,7 @@ ALGO_SHAPES = [
 
 
 @pytest.mark.parametrize("sh", ALGO_SHAPES, ids=_id)
-@pytest.mark.parametrize("algo", [B.GBCONV_ALGO_IM2COL, B.GBCONV_ALGO_SHIFT])
+@pytest.mark.parametrize("algo", [B.GBCONV_ALGO_IM2COL, B.GBCONV_ALGO_SHIFT, B.GBCONV_ALGO_SHIFT_T])
 @pytest.mark.parametrize("block_n", [64, 128])
 def test_bf16_forward_algorithms(sh, algo, block_n):
     prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
@@ -270,6 +270,33 @@ def test_bf16_forward_algorithms(sh, algo, block_n):
     finally:
         B.gbconv_shutdown()
     assert r["err_i"] <= TOL_ACC32, r["err_i"]
+
+
+T_SHAPES = [  # the transposed band kernel: K <= 128, both output-channel tiles
+    ConvShape(2, 64, 9, 11, 64, 3, 3, 1, 1, 1),
+    ConvShape(2, 64, 10, 10, 40, 3, 3, 1, 1, 1),      # K < 64: clipped channels
+    ConvShape(2, 128, 9, 9, 128, 3, 3, 1, 1, 1),      # two channel blocks, 128 channels
+    ConvShape(1, 64, 12, 12, 96, 5, 5, 1, 2, 1),      # 96 channels on a 128 tile
+    ConvShape(2, 32, 20, 30, 64, 3, 3, 1, 2, 2),      # dilation 2
+    ConvShape(1, 64, 5, 120, 64, 3, 3, 1, 1, 1),      # Wx = 128, two rows per tile
+    ConvShape(1, 64, 4, 150, 32, 1, 3, 1, (0, 1), 1),  # Wx = 256, one row per tile
+]
+
+
+@pytest.mark.parametrize("sh", T_SHAPES, ids=_id)
+@pytest.mark.parametrize("out", ["bf16", "f32"])
+def test_bf16_transposed_band_kernel(sh, out):
+    od = B.GBCONV_F32 if out == "f32" else B.GBCONV_BF16
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                     B.GBCONV_BF16, od, B.GBCONV_NHWC, B.GBCONV_FLAG_BIAS | B.GBCONV_FLAG_RELU)
+    B.check(B.gbconv_set_config(B.GBCONV_OP_FWD, prob,
+                                B.gbconv_config_t(64, 0, 0, 0, B.GBCONV_ALGO_SHIFT_T)), "set_config")
+    try:
+        r = fwd_case(sh, torch.bfloat16, out_dtype=torch.float32 if out == "f32" else None,
+                     relu=True, seed=72)
+    finally:
+        B.gbconv_shutdown()
+    assert r["err_i"] <= (TOL_ACC32 if out == "f32" else TOL_BF16_OUT), r["err_i"]
 
 
 @pytest.mark.parametrize("algo", [B.GBCONV_ALGO_IM2COL, B.GBCONV_ALGO_SHIFT])
