@@ -25,11 +25,13 @@
 //  * Epilogue: 8 warps, two groups of four (one warp per TMEM lane quarter).
 //    Group g takes 32-position chunks j = g, g+2, ... Each thread holds one
 //    output channel k (bias and FP8 scale are per-thread constants) and 32
-//    positions; pairs of lanes exchange values so that each writes 32-bit
-//    words of two adjacent channels into a [32 positions][KT channels] BF16
-//    (or FP32) tile in shared memory (128-byte swizzled rows). A named barrier
-//    joins the group, then one thread stores the tile with TMA through a 3-D
-//    map of y as [N*P][Q][K] (positions q >= Q and channels >= K clipped).
+//    positions (KT = 128, 32x32b loads) or 16 (KT = 64, 16x32bx2 loads: the
+//    M = 64 accumulator fills lanes 0-15 only, so two threads split each
+//    channel's positions). Each value goes as one 16-bit (or 32-bit) store
+//    into a [32 positions][KT channels] tile in shared memory (128-byte
+//    swizzled rows). A named barrier joins the group, then one thread stores
+//    the tile with TMA through a 3-D map of y as [N*P][Q][K] (positions
+//    q >= Q and channels >= K clipped).
 //
 // Warp roles and bounded waits as in tc_fwd.cu (320 threads).
 #include <cuda_bf16.h>
@@ -75,11 +77,6 @@ __device__ __forceinline__ void tdecode(const TParams &p, int tile, int &n, int 
 
 __device__ __forceinline__ void named_bar(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
 }
 
 template <int KT, bool FP8>
@@ -318,7 +315,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
         const int quarter = warp & 3;       // TMEM lane quarter
         const int group = ew >> 2;          // chunks j with j % 2 == group
         // this thread's output-channel row within the tile (valid lanes only)
-        const bool lane_ok = KT == 128 || lane < 16;
+        // KT = 128: lane = channel; KT = 64 (two-half loads): lanes l and l+16
+        // share channel l and split the chunk's positions
         const int krow = quarter * KPW + (KT == 128 ? lane : (lane & 15));
         uint8_t *gbuf = sEpi + group * 2 * STAGE_T;
         int ebuf = 0;
@@ -337,66 +335,59 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
             ptx::tc_fence_after();
             const int k = kt * KT + krow;
             float scl = 1.f, bia = 0.f;
-            if (lane_ok && k < prm.K) {
+            if (k < prm.K) {
                 if (FP8) scl = xs * __ldg(prm.w_scale + k);
                 if (prm.bias) bia = __ldg(prm.bias + k);
             }
             for (int j = group; j < NPOS / 32; j += 2) {
-                uint32_t v[32];
-                ptx::tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
-                                            (uint32_t)(acc * NPOS + j * 32),
-                                        v);
+                // NV values per thread: KT = 128: lane = channel, 32 positions;
+                // KT = 64: lanes 0-15 positions 0-15, lanes 16-31 positions 16-31
+                constexpr int NV = KT == 128 ? 32 : 16;
+                uint32_t v[NV];
+                const uint32_t ta = tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                                    (uint32_t)(acc * NPOS + j * 32);
+                if constexpr (KT == 128)
+                    ptx::tmem_ld_32x32b_x32(ta, *reinterpret_cast<uint32_t(*)[32]>(v));
+                else
+                    ptx::tmem_ld_16x32bx2_x16(ta, *reinterpret_cast<uint32_t(*)[16]>(v));
                 ptx::tmem_ld_wait();
                 if (j + 2 >= NPOS / 32) {
                     ptx::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
                 }
-                // chunk j = positions 32j .. 32j+31 = output row p, columns q0..q0+31
                 const int p = p0 + ((32 * j) >> prm.wx_log2);
                 const int q0 = (32 * j) & wx_mask;
-                const bool store = p < prm.P && q0 < prm.Q;  // warp-uniform
-                float f[32];
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    float a = __uint_as_float(v[i]);
-                    if (FP8) a = a * scl;
-                    a = a + bia;
-                    if (prm.relu) a = fmaxf(a, 0.f);
-                    f[i] = a;
-                }
+                const bool store = p < prm.P && q0 < prm.Q;
+                const int e0 = KT == 128 ? 0 : (lane >> 4) * 16;   // first position of this thread
                 uint8_t *buf = gbuf + ebuf * STAGE_T;
                 if (store) {
-                    // staging tile [32 positions][KT channels]: 64-channel halves of
-                    // 128-byte rows (BF16) or 32-channel quarters (FP32), each
-                    // 32 rows x 128 B with the 128-byte swizzle (unit u ^ (row & 7))
                     if (threadIdx.x == 64 + group * 128) ptx::bulk_wait_read<1>();
                     named_bar(1 + group, 128);
                     if (!prm.out_f32) {
-                        // lanes 2i / 2i+1 hold channels k, k+1: exchange so that the
-                        // even lane writes (k, k+1) of even positions, the odd lane of odd ones
+                        const int half = krow >> 6, kb = (krow & 63) * 2;
+                        uint8_t *hb = buf + half * 4096 + (kb & 15);
 #pragma unroll
-                        for (int i = 0; i < 32; i += 2) {
-                            const float o0 = __shfl_xor_sync(0xffffffffu, f[i], 1);
-                            const float o1 = __shfl_xor_sync(0xffffffffu, f[i + 1], 1);
-                            const bool odd = lane & 1;
-                            const int e = odd ? i + 1 : i;
-                            const uint32_t word = odd ? pack2(o1, f[i + 1]) : pack2(f[i], o0);
-                            const int kc = krow & ~1;              // even channel of the pair
-                            const int half = kc >> 6, kb = (kc & 63) * 2;
-                            uint8_t *row = buf + half * 4096 + e * 128;
-                            if (lane_ok)
-                                *reinterpret_cast<uint32_t *>(
-                                    row + ((((kb >> 4) ^ (e & 7)) << 4) | (kb & 15))) = word;
+                        for (int i = 0; i < NV; ++i) {
+                            float a = __uint_as_float(v[i]);
+                            if (FP8) a = a * scl;
+                            a = a + bia;
+                            if (prm.relu) a = fmaxf(a, 0.f);
+                            const int e = e0 + i;
+                            *reinterpret_cast<__nv_bfloat16 *>(
+                                hb + e * 128 + (((kb >> 4) ^ (e & 7)) << 4)) = __float2bfloat16_rn(a);
                         }
                     } else {
+                        const int qd = krow >> 5, kb = (krow & 31) * 4;
+                        uint8_t *hb = buf + qd * 4096 + (kb & 15);
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            const int qd = krow >> 5, kb = (krow & 31) * 4;
-                            uint8_t *row = buf + qd * 4096 + e * 128;
-                            if (lane_ok)
-                                *reinterpret_cast<float *>(
-                                    row + ((((kb >> 4) ^ (e & 7)) << 4) | (kb & 15))) = f[e];
+                        for (int i = 0; i < NV; ++i) {
+                            float a = __uint_as_float(v[i]);
+                            if (FP8) a = a * scl;
+                            a = a + bia;
+                            if (prm.relu) a = fmaxf(a, 0.f);
+                            const int e = e0 + i;
+                            *reinterpret_cast<float *>(hb + e * 128 + (((kb >> 4) ^ (e & 7)) << 4)) = a;
                         }
                     }
                     ptx::fence_proxy_async_smem();
