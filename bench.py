@@ -41,6 +41,34 @@ def peaks():
         return dict(PEAKS_FALLBACK), "fallback"
 
 
+def csrc_sha1():
+    import glob
+    import hashlib
+    d = os.path.join(ROOT, "paper_2207_00257_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh")) +
+                   glob.glob(os.path.join(d, "*.h")))
+    h = hashlib.sha1()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(tag):
+    """DRAM bytes (read + write) per launch of this layer's kernel from the
+    committed ncu record, or None if the kernel sources changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_dram_traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("csrc_sha1") != csrc_sha1() or tag not in rec.get("per_launch", {}):
+        return None
+    r = rec["per_launch"][tag]
+    return r["dram_read"] + r["dram_write"]
+
+
 # ---------------------------------------------------------------------------
 # clocks sampling (nvidia-smi) during the measured region
 # ---------------------------------------------------------------------------
@@ -310,7 +338,7 @@ def run_ours(args, rank, world, local):
     else:
         roof = {"bound": "hbm", "achieved": dom["gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(dom["gbs"] / pk["hbm_gbs"], 4)}
-    roof.update({"kernel": f"tc_fwd_kernel ({sh.tag})", "traffic": None,
+    roof.update({"kernel": f"forward kernel of {sh.tag}", "traffic": ncu_traffic(sh.tag),
                  "algorithmic_bytes_per_launch": layer_bytes(sh, 2, 2),
                  "flops_per_launch": sh.flops, "peak_source": pk_kind + " (burst)"})
     clocks_window = (res["t0"], res["t1"])
