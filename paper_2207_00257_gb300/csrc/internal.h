@@ -90,8 +90,11 @@ gbconv_status_t launch_tc_wgrad_partials(const Dims &d, const TcConfig &cfg, con
 // tmap.cpp: tensor-map encoding through the driver entry points.
 gbconv_status_t encode_im2col_act(CUtensorMap *m, const Dims &d, const void *x, int elem_bytes,
                                   int channels_per_pixel, int pixels_per_column);
+// Tiled map; elem_strides (may be null = all 1) is the traversal step per
+// dimension: a box of b elements with step t loads ceil(b / t) of them.
 gbconv_status_t encode_tiled(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *ptr,
                              const uint64_t *dims, const uint64_t *strides_bytes,
-                             const uint32_t *box, CUtensorMapSwizzle swz);
+                             const uint32_t *box, CUtensorMapSwizzle swz,
+                             const uint32_t *elem_strides = nullptr);
 
 }  // namespace gbc

@@ -477,9 +477,12 @@ gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void 
     TcConfig cfg = cfg_in;
     if (cfg.block_n != 32 && cfg.block_n != 64 && cfg.block_n != 128 && cfg.block_n != 256)
         return GBCONV_ERR_INVALID_ARG;
-    // Automatic choice: the shifted-band kernel for stride-1 layers with more
-    // than one filter tap whose filter fits in shared memory (a 1x1 layer
-    // gains nothing from it and would compute the extended rows' spare columns).
+    // Automatic choice: for layers with more than one filter tap, the
+    // transposed band kernel when the output channels fit one 128-row MMA
+    // (any stride up to 4, by phase decomposition), else the shifted-band
+    // kernel for stride-1 layers whose filter fits in shared memory. A 1x1
+    // layer gains nothing from a band and would compute the extended rows'
+    // spare columns.
     if (cfg.algo == GBCONV_ALGO_SHIFT_T || (cfg.algo == GBCONV_ALGO_AUTO && d.R * d.S > 1)) {
         if (tc_fwd_t_tile(d))
             return launch_tc_fwd_t(d, x, w, bias, x_scale, w_scale, y, st);

@@ -1,11 +1,11 @@
-// tc_fwd_t.cu -- "transposed" shifted-band forward convolution for stride-1
-// layers with at most 128 output channels.
+// tc_fwd_t.cu -- "transposed" shifted-band forward convolution for layers
+// with at most 128 output channels and strides up to 4.
 //
-// Same operation and input band as tc_fwd_shift.cu (one padded input band per
-// channel block, every filter tap a row shift of it; forward pass of a
-// convolutional layer, paper Sec. 5.B), but the GEMM is computed transposed:
+// Same idea as tc_fwd_shift.cu (one padded input band per channel block, every
+// filter tap a row shift of it; forward pass of a convolutional layer, paper
+// Sec. 5.B), but the GEMM is computed transposed:
 //
-//   D^T[k][e] = sum_{(r,s), c} W[k][(r,s)][c] * band[e + r*dh*Wx + s*dw][c]
+//   D^T[k][e] = sum_{(r,s), c} W[k][(r,s)][c] * band[e + shift(r,s)][c]
 //
 // with M = KT output channels (64 or 128) and N = 256 extended output
 // positions per tcgen05.mma. On GB300 one MMA instruction costs about the
@@ -13,24 +13,37 @@
 // with 64 or 128 output channels runs 1.6-1.8x more tensor work per
 // instruction this way than with pixels on M.
 //
-//  * Tile: 256 consecutive extended positions = TR = 256 / Wx output rows of
-//    one image, times KT output channels.
+//  * Strides by phase decomposition. Tap (r, s) of output (p, q) reads input
+//    row u*p - ph + r*dh = u*(p + i) + a - ph with a = (r*dh) mod u,
+//    i = (r*dh) div u, and likewise column v*(q + j) + b - pw. So the taps
+//    split into u*v phases (a, b); within a phase every tap is the shift
+//    (i, j) of one phase image X_ab[p'][q'] = x[u*p' + a - ph][v*q' + b - pw].
+//    One band of a phase image is one TMA box with element strides (v, u)
+//    over x. Stride 1 is the single phase (0, 0). A host-built table lists
+//    the taps phase by phase (filter tap index, band row shift i*Wx + j);
+//    phases without taps are skipped.
+//  * Tile: TR output rows of one image as TR * Wx consecutive extended
+//    positions (Wx = power of two >= Q + max j; TR <= 256 / Wx, chosen to
+//    split the P rows into equal tiles), times KT output channels.
 //  * A operand: filter tile W[(r,s), c block] = KT rows of 128 bytes, resident
-//    in shared memory when the whole filter fits, otherwise streamed.
+//    in shared memory when the whole filter fits, otherwise streamed in
+//    table order.
 //  * B operand: 256 band rows starting at the tap's shift (K-major, 128-byte
 //    swizzle; any 128-byte row is a valid start).
 //  * TMEM: two 256-column accumulators. For M = 128 row k of D^T sits in lane
 //    k; for M = 64 row k sits in lane 32*(k/16) + k%16 (lanes 16-31 of each
 //    quarter unused).
 //  * Epilogue: 8 warps, two groups of four (one warp per TMEM lane quarter).
-//    Group g takes 32-position chunks j = g, g+2, ... Each thread holds one
-//    output channel k (bias and FP8 scale are per-thread constants) and 32
-//    positions (KT = 128, 32x32b loads) or 16 (KT = 64, 16x32bx2 loads: the
-//    M = 64 accumulator fills lanes 0-15 only, so two threads split each
-//    channel's positions). Each value goes as one 16-bit (or 32-bit) store
-//    into a [32 positions][KT channels] tile in shared memory (128-byte
-//    swizzled rows). A named barrier joins the group, then one thread stores
-//    the tile with TMA through a 3-D map of y as [N*P][Q][K] (positions
+//    Group g takes 32-position chunks j = g, g+2, ... BF16 output: each warp
+//    reads its channels x 32 positions with 16x256b loads (the accumulator
+//    fragment layout: a thread holds two channels x two adjacent positions
+//    per 8-column group; for M = 64 the accumulator fills lanes 0-15 of each
+//    quarter), packs position pairs to bf16x2 and writes them with
+//    stmatrix.trans as position rows of 8 channels into a [32 positions][KT
+//    channels] tile in shared memory (128-byte swizzled rows). FP32 output:
+//    one channel row per thread (32x32b / 16x32bx2 loads), one 32-bit store
+//    per value. A named barrier joins the group, then one thread stores the
+//    tile with TMA through a 3-D map of y as [N*P][Q][K] (positions
 //    q >= Q and channels >= K clipped).
 //
 // Warp roles and bounded waits as in tc_fwd.cu (320 threads).
@@ -46,27 +59,37 @@
 namespace gbc {
 namespace {
 
-constexpr int NPOS = 256;  // positions per tile (MMA N)
+constexpr int NPOS = 256;  // accumulator columns per tile (largest MMA N)
 constexpr int NTHREADS = 320;
 constexpr int EPI_WARPS = 8;
 constexpr int SMEM_ALIGN = 1024;
 constexpr int BAR_BYTES = 512;
 constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr int MAX_SA = 4, MAX_SB = 12;
+constexpr int MAX_STRIDE = 4;
+constexpr int MAX_PHASES = MAX_STRIDE * MAX_STRIDE;
+constexpr int MAX_TAPS = 128;
 
 struct TParams {
-    CUtensorMap tmX;  // x [N][H][W][C], box {KE, Wx, nr, 1}
+    CUtensorMap tmX;  // x [N][H][W][C], box {KE, v*Wx, u*nr, 1}, element strides {1, v, u, 1}
     CUtensorMap tmW;  // w [K][R*S][C], box {KE, 1, KT}
     CUtensorMap tmY;  // y [N*P][Q][K], box {64 (BF16) | 32 (FP32), 32, 1}
     int N, P, Q, K;
-    int pw, ph, dh, dw, S, RS;
-    int wx_log2, TR;
+    int u, RS;
+    int wx_log2, TR, n_pos;  // n_pos = TR * Wx positions per tile (MMA N)
+    // phase f: band origin (column b - pw, row offset a - ph), taps [end[f-1], end[f])
+    int n_phase;
+    int ph_w0[MAX_PHASES], ph_h0[MAX_PHASES], ph_end[MAX_PHASES];
+    uint16_t tap_t[MAX_TAPS];      // filter tap index r*S + s
+    uint16_t tap_shift[MAX_TAPS];  // band row offset i*Wx + j
     int c_blocks, k_tiles, p_tiles, num_tiles;
     int band_bytes, band_stride, w_resident, stages_a, stages_b;
     int relu, out_f32;
     const float *bias, *x_scale, *w_scale;
     Guard guard;
 };
+
+static_assert(sizeof(TParams) <= 4096, "transposed kernel parameters too large");
 
 __device__ __forceinline__ void tdecode(const TParams &p, int tile, int &n, int &p0, int &kt) {
     kt = tile % p.k_tiles;
@@ -166,37 +189,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                 int n, p0, kt;
                 tdecode(prm, tile, n, p0, kt);
                 for (int cb = 0; ok && cb < prm.c_blocks; ++cb) {
-                    if (!ptx::mbar_wait(&emptyA[sa], pa ^ 1, lim, abort_flag)) {
-                        fail();
-                        ok = false;
-                        break;
-                    }
-                    if (!skip) {
-                        ptx::mbar_arrive_expect_tx(&fullA[sa], (uint32_t)prm.band_bytes);
-                        ptx::tma_load_4d(sA + sa * prm.band_stride, &prm.tmX, &fullA[sa], cb * KE,
-                                         -prm.pw, p0 - prm.ph, n);
-                        ++issued_a;
-                    }
-                    if (++sa == SA) {
-                        sa = 0;
-                        pa ^= 1;
-                    }
-                    if (prm.w_resident) continue;
-                    for (int t = 0; t < prm.RS; ++t) {
-                        if (!ptx::mbar_wait(&emptyW[sb], pb ^ 1, lim, abort_flag)) {
+                    for (int f = 0; ok && f < prm.n_phase; ++f) {
+                        if (!ptx::mbar_wait(&emptyA[sa], pa ^ 1, lim, abort_flag)) {
                             fail();
                             ok = false;
                             break;
                         }
                         if (!skip) {
-                            ptx::mbar_arrive_expect_tx(&fullW[sb], (uint32_t)W_TILE);
-                            ptx::tma_load_3d(sW + sb * W_TILE, &prm.tmW, &fullW[sb], cb * KE, t,
-                                             kt * KT);
-                            ++issued_b;
+                            ptx::mbar_arrive_expect_tx(&fullA[sa], (uint32_t)prm.band_bytes);
+                            ptx::tma_load_4d(sA + sa * prm.band_stride, &prm.tmX, &fullA[sa], cb * KE,
+                                             prm.ph_w0[f], prm.u * p0 + prm.ph_h0[f], n);
+                            ++issued_a;
                         }
-                        if (++sb == SB) {
-                            sb = 0;
-                            pb ^= 1;
+                        if (++sa == SA) {
+                            sa = 0;
+                            pa ^= 1;
+                        }
+                        if (prm.w_resident) continue;
+                        for (int ti = f ? prm.ph_end[f - 1] : 0; ti < prm.ph_end[f]; ++ti) {
+                            if (!ptx::mbar_wait(&emptyW[sb], pb ^ 1, lim, abort_flag)) {
+                                fail();
+                                ok = false;
+                                break;
+                            }
+                            if (!skip) {
+                                ptx::mbar_arrive_expect_tx(&fullW[sb], (uint32_t)W_TILE);
+                                ptx::tma_load_3d(sW + sb * W_TILE, &prm.tmW, &fullW[sb], cb * KE,
+                                                 prm.tap_t[ti], kt * KT);
+                                ++issued_b;
+                            }
+                            if (++sb == SB) {
+                                sb = 0;
+                                pb ^= 1;
+                            }
                         }
                     }
                 }
@@ -236,7 +261,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                 fail();
                 ok = false;
             }
-            uint32_t idesc = FP8 ? ptx::idesc_e4m3(NPOS) : ptx::idesc_bf16(NPOS);
+            uint32_t idesc = FP8 ? ptx::idesc_e4m3(prm.n_pos) : ptx::idesc_bf16(prm.n_pos);
             idesc = (idesc & ~(0x1Fu << 24)) | ((uint32_t)(KT >> 4) << 24);  // M = KT
             int sa = 0, sb = 0;
             uint32_t pa = 0, pb = 0;
@@ -250,56 +275,54 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                 }
                 ptx::tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * NPOS);
+                uint32_t accum = 0;
                 for (int cb = 0; ok && cb < prm.c_blocks; ++cb) {
-                    if (!ptx::mbar_wait(&fullA[sa], pa, lim, abort_flag)) {
-                        fail();
-                        ok = false;
-                        break;
-                    }
-                    ptx::tc_fence_after();
-                    const uint32_t band = ptx::smem_addr(sA + sa * prm.band_stride);
-                    int r = 0, s = 0;
-                    for (int t = 0; t < prm.RS; ++t) {
-                        uint32_t w_addr;
-                        if (prm.w_resident) {
-                            w_addr = ptx::smem_addr(sW + (cb * prm.RS + t) * W_TILE);
-                        } else {
-                            if (!ptx::mbar_wait(&fullW[sb], pb, lim, abort_flag)) {
-                                fail();
-                                ok = false;
-                                break;
-                            }
-                            ptx::tc_fence_after();
-                            w_addr = ptx::smem_addr(sW + sb * W_TILE);
+                    for (int f = 0; f < prm.n_phase; ++f) {
+                        if (!ptx::mbar_wait(&fullA[sa], pa, lim, abort_flag)) {
+                            fail();
+                            ok = false;
+                            break;
                         }
-                        const uint32_t shift = (uint32_t)(((r * prm.dh) << prm.wx_log2) + s * prm.dw);
-                        const uint64_t ad = ptx::sdesc_kmajor_sw128(w_addr);
-                        const uint64_t bd = ptx::sdesc_kmajor_sw128(band + shift * 128u);
+                        ptx::tc_fence_after();
+                        const uint32_t band = ptx::smem_addr(sA + sa * prm.band_stride);
+                        for (int ti = f ? prm.ph_end[f - 1] : 0; ti < prm.ph_end[f]; ++ti) {
+                            uint32_t w_addr;
+                            if (prm.w_resident) {
+                                w_addr = ptx::smem_addr(sW + (cb * prm.RS + prm.tap_t[ti]) * W_TILE);
+                            } else {
+                                if (!ptx::mbar_wait(&fullW[sb], pb, lim, abort_flag)) {
+                                    fail();
+                                    ok = false;
+                                    break;
+                                }
+                                ptx::tc_fence_after();
+                                w_addr = ptx::smem_addr(sW + sb * W_TILE);
+                            }
+                            const uint64_t ad = ptx::sdesc_kmajor_sw128(w_addr);
+                            const uint64_t bd =
+                                ptx::sdesc_kmajor_sw128(band + (uint32_t)prm.tap_shift[ti] * 128u);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const uint32_t accum = (cb | t | k) != 0;
-                            if (FP8)
-                                ptx::mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, accum);
-                            else
-                                ptx::mma_f16(d, ad + 2 * k, bd + 2 * k, idesc, accum);
-                        }
-                        if (!prm.w_resident) {
-                            ptx::mma_commit(&emptyW[sb]);
-                            if (++sb == SB) {
-                                sb = 0;
-                                pb ^= 1;
+                            for (int k = 0; k < 4; ++k) {
+                                if (FP8)
+                                    ptx::mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                                else
+                                    ptx::mma_f16(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                                accum = 1;
+                            }
+                            if (!prm.w_resident) {
+                                ptx::mma_commit(&emptyW[sb]);
+                                if (++sb == SB) {
+                                    sb = 0;
+                                    pb ^= 1;
+                                }
                             }
                         }
-                        if (++s == prm.S) {
-                            s = 0;
-                            ++r;
+                        if (!ok) break;
+                        ptx::mma_commit(&emptyA[sa]);
+                        if (++sa == SA) {
+                            sa = 0;
+                            pa ^= 1;
                         }
-                    }
-                    if (!ok) break;
-                    ptx::mma_commit(&emptyA[sa]);
-                    if (++sa == SA) {
-                        sa = 0;
-                        pa ^= 1;
                     }
                 }
                 if (!ok) break;
@@ -318,6 +341,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
         // KT = 128: lane = channel; KT = 64 (two-half loads): lanes l and l+16
         // share channel l and split the chunk's positions
         const int krow = quarter * KPW + (KT == 128 ? lane : (lane & 15));
+        constexpr int NH = KT / 64;              // 16-lane loads per chunk (BF16 output)
+        const int chb0 = quarter * KPW;          // first channel of this warp's lane quarter
         uint8_t *gbuf = sEpi + group * 2 * STAGE_T;
         int ebuf = 0;
         const int wx_mask = (1 << prm.wx_log2) - 1;
@@ -333,25 +358,43 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                 break;
             }
             ptx::tc_fence_after();
-            const int k = kt * KT + krow;
+            // FP32 output: one channel row per thread (krow)
             float scl = 1.f, bia = 0.f;
-            if (k < prm.K) {
-                if (FP8) scl = xs * __ldg(prm.w_scale + k);
-                if (prm.bias) bia = __ldg(prm.bias + k);
+            // BF16 output: 16-lane loads h, thread t holds channels chb(h) + t/4 + 8s
+            float bs[NH][2], ss[NH][2];
+            if (prm.out_f32) {
+                const int k = kt * KT + krow;
+                if (k < prm.K) {
+                    if (FP8) scl = xs * __ldg(prm.w_scale + k);
+                    if (prm.bias) bia = __ldg(prm.bias + k);
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < NH; ++h)
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        const int k = kt * KT + chb0 + 16 * h + 8 * s2 + (lane >> 2);
+                        bs[h][s2] = (prm.bias && k < prm.K) ? __ldg(prm.bias + k) : 0.f;
+                        ss[h][s2] = (FP8 && k < prm.K) ? xs * __ldg(prm.w_scale + k) : 1.f;
+                    }
             }
-            for (int j = group; j < NPOS / 32; j += 2) {
-                // NV values per thread: KT = 128: lane = channel, 32 positions;
-                // KT = 64: lanes 0-15 positions 0-15, lanes 16-31 positions 16-31
-                constexpr int NV = KT == 128 ? 32 : 16;
-                uint32_t v[NV];
+            const int nchunks = prm.n_pos >> 5;
+            for (int j = group; j < nchunks; j += 2) {
+                uint32_t v[32];
                 const uint32_t ta = tmem_base + ((uint32_t)(quarter * 32) << 16) +
                                     (uint32_t)(acc * NPOS + j * 32);
-                if constexpr (KT == 128)
+                if (!prm.out_f32) {
+                    // accumulator-fragment layout, 16 channels x 32 positions per load
+                    ptx::tmem_ld_16x256b_x4(ta, *reinterpret_cast<uint32_t(*)[16]>(v));
+                    if constexpr (KT == 128)
+                        ptx::tmem_ld_16x256b_x4(ta + (16u << 16), *reinterpret_cast<uint32_t(*)[16]>(v + 16));
+                } else if constexpr (KT == 128) {
                     ptx::tmem_ld_32x32b_x32(ta, *reinterpret_cast<uint32_t(*)[32]>(v));
-                else
+                } else {
                     ptx::tmem_ld_16x32bx2_x16(ta, *reinterpret_cast<uint32_t(*)[16]>(v));
+                }
                 ptx::tmem_ld_wait();
-                if (j + 2 >= NPOS / 32) {
+                if (j + 2 >= nchunks) {
                     ptx::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
@@ -359,25 +402,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                 const int p = p0 + ((32 * j) >> prm.wx_log2);
                 const int q0 = (32 * j) & wx_mask;
                 const bool store = p < prm.P && q0 < prm.Q;
-                const int e0 = KT == 128 ? 0 : (lane >> 4) * 16;   // first position of this thread
                 uint8_t *buf = gbuf + ebuf * STAGE_T;
                 if (store) {
                     if (threadIdx.x == 64 + group * 128) ptx::bulk_wait_read<1>();
                     named_bar(1 + group, 128);
                     if (!prm.out_f32) {
-                        const int half = krow >> 6, kb = (krow & 63) * 2;
-                        uint8_t *hb = buf + half * 4096 + (kb & 15);
+                        // Register 4g + 2s (+1) of load h: channel chb0 + 16h + 8s + t/4,
+                        // positions 8g + 2(t%4) (+1). Each packed pair is one row of an
+                        // 8x8 (channel x position) matrix; stmatrix.trans writes it as
+                        // 8 position rows of 8 channels (16 bytes) into the swizzled tile.
+                        const int mrow = lane & 7, msel = lane >> 3;
 #pragma unroll
-                        for (int i = 0; i < NV; ++i) {
-                            float a = __uint_as_float(v[i]);
-                            if (FP8) a = a * scl;
-                            a = a + bia;
-                            if (prm.relu) a = fmaxf(a, 0.f);
-                            const int e = e0 + i;
-                            *reinterpret_cast<__nv_bfloat16 *>(
-                                hb + e * 128 + (((kb >> 4) ^ (e & 7)) << 4)) = __float2bfloat16_rn(a);
-                        }
+                        for (int h = 0; h < NH; ++h)
+#pragma unroll
+                            for (int gp = 0; gp < 2; ++gp) {
+                                uint32_t pk[4];
+#pragma unroll
+                                for (int m = 0; m < 4; ++m) {
+                                    const int g = 2 * gp + (m >> 1), s2 = m & 1;
+                                    float a0 = __uint_as_float(v[16 * h + 4 * g + 2 * s2]);
+                                    float a1 = __uint_as_float(v[16 * h + 4 * g + 2 * s2 + 1]);
+                                    if (FP8) {
+                                        a0 = a0 * ss[h][s2];
+                                        a1 = a1 * ss[h][s2];
+                                    }
+                                    a0 = a0 + bs[h][s2];
+                                    a1 = a1 + bs[h][s2];
+                                    if (prm.relu) {
+                                        a0 = fmaxf(a0, 0.f);
+                                        a1 = fmaxf(a1, 0.f);
+                                    }
+                                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(a0, a1);
+                                    pk[m] = *reinterpret_cast<const uint32_t *>(&b2);
+                                }
+                                const int e = 8 * (2 * gp + (msel >> 1)) + mrow;   // position
+                                const int ch = chb0 + 16 * h + 8 * (msel & 1);    // first channel
+                                const uint32_t addr = ptx::smem_addr(
+                                    buf + (ch >> 6) * 4096 + e * 128 + ((((ch & 63) >> 3) ^ (e & 7)) << 4));
+                                ptx::stmatrix_x4_trans(addr, pk[0], pk[1], pk[2], pk[3]);
+                            }
                     } else {
+                        const int e0 = KT == 128 ? 0 : (lane >> 4) * 16;  // first position of this thread
+                        constexpr int NV = KT == 128 ? 32 : 16;
                         const int qd = krow >> 5, kb = (krow & 31) * 4;
                         uint8_t *hb = buf + qd * 4096 + (kb & 15);
 #pragma unroll
@@ -417,6 +483,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
 
 struct TPlan {
     int wx_log2, TR, nr, band_bytes, band_stride, c_blocks, w_resident, stages_a, stages_b;
+    int n_phase;
 };
 
 int ilog2(int v) {
@@ -428,23 +495,46 @@ int ilog2(int v) {
 template <int KT>
 constexpr int epi_total() { return 2 * 2 * 32 * KT * 4; }
 
+// Largest band shift of the phase decomposition: i = (r*dh) div u over the
+// rows, j = (s*dw) div v over the columns.
+int max_shift(int taps, int dil, int stride) { return ((taps - 1) * dil) / stride; }
+
+int count_phases(const Dims &d) {
+    bool used[MAX_PHASES] = {};
+    int n = 0;
+    for (int r = 0; r < d.R; ++r)
+        for (int s = 0; s < d.S; ++s) {
+            const int f = ((r * d.dh) % d.u) * d.v + (s * d.dw) % d.v;
+            if (!used[f]) {
+                used[f] = true;
+                ++n;
+            }
+        }
+    return n;
+}
+
 bool make_plan(const Dims &d, int kt, TPlan *pl) {
-    if (d.u != 1 || d.v != 1) return false;
+    if (d.u > MAX_STRIDE || d.v > MAX_STRIDE || d.R * d.S > MAX_TAPS) return false;
     const bool fp8 = d.in_dtype == GBCONV_E4M3;
     const int ke = fp8 ? 128 : 64;
-    const int need = d.Q + (d.S - 1) * d.dw;
+    const int imax = max_shift(d.R, d.dh, d.u), jmax = max_shift(d.S, d.dw, d.v);
+    const int need = d.Q + jmax;
     int wx = 32;
     while (wx < need) wx *= 2;
-    if (wx > NPOS) return false;
+    if (wx > NPOS || wx * d.v > 256) return false;  // TMA box extent <= 256
     TPlan p{};
     p.wx_log2 = ilog2(wx);
-    p.TR = NPOS / wx;
-    p.nr = p.TR + (d.R - 1) * d.dh;
-    if (p.nr > 256) return false;
+    // rows per tile: at most 256 / Wx, spread evenly over the output rows
+    const int tr_max = NPOS / wx;
+    const int row_tiles = std::max(1, (d.P + tr_max - 1) / tr_max);
+    p.TR = std::max(1, (d.P + row_tiles - 1) / row_tiles);
+    p.nr = p.TR + imax;
+    if (p.nr * d.u > 256) return false;
     p.band_bytes = 128 * wx * p.nr;
-    p.band_stride = (p.band_bytes + (d.S - 1) * d.dw * 128 + 1023) / 1024 * 1024;
+    p.band_stride = (p.band_bytes + jmax * 128 + 1023) / 1024 * 1024;
     if (p.band_stride > 80 * 1024) return false;
     p.c_blocks = (d.C + ke - 1) / ke;
+    p.n_phase = count_phases(d);
     const int epi = kt == 128 ? epi_total<128>() : epi_total<64>();
     const int budget = SMEM_LIMIT - SMEM_ALIGN - BAR_BYTES - epi;
     const int wtile = kt * 128;
@@ -462,6 +552,32 @@ bool make_plan(const Dims &d, int kt, TPlan *pl) {
     }
     *pl = p;
     return true;
+}
+
+// Tap table: taps grouped by phase (a, b), phases in order f = a*v + b,
+// phases without taps left out.
+void build_taps(const Dims &d, int wx_log2, TParams *prm) {
+    int n = 0, f_out = 0;
+    for (int a = 0; a < d.u; ++a)
+        for (int b = 0; b < d.v; ++b) {
+            const int start = n;
+            for (int r = 0; r < d.R; ++r) {
+                if ((r * d.dh) % d.u != a) continue;
+                for (int s = 0; s < d.S; ++s) {
+                    if ((s * d.dw) % d.v != b) continue;
+                    const int i = (r * d.dh) / d.u, j = (s * d.dw) / d.v;
+                    prm->tap_t[n] = (uint16_t)(r * d.S + s);
+                    prm->tap_shift[n] = (uint16_t)((i << wx_log2) + j);
+                    ++n;
+                }
+            }
+            if (n == start) continue;
+            prm->ph_w0[f_out] = b - d.pw;
+            prm->ph_h0[f_out] = a - d.ph;
+            prm->ph_end[f_out] = n;
+            ++f_out;
+        }
+    prm->n_phase = f_out;
 }
 
 template <int KT, bool FP8>
@@ -502,8 +618,10 @@ gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, con
     memset(&prm, 0, sizeof(prm));
     uint64_t xd[4] = {(uint64_t)d.C, (uint64_t)d.W, (uint64_t)d.H, (uint64_t)d.N};
     uint64_t xs[3] = {(uint64_t)d.C * eb, (uint64_t)d.W * d.C * eb, (uint64_t)d.H * d.W * d.C * eb};
-    uint32_t xb[4] = {(uint32_t)ke, (uint32_t)(1 << pl.wx_log2), (uint32_t)pl.nr, 1};
-    gbconv_status_t s = encode_tiled(&prm.tmX, in_t, 4, x, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_128B);
+    uint32_t xb[4] = {(uint32_t)ke, (uint32_t)(d.v << pl.wx_log2), (uint32_t)(d.u * pl.nr), 1};
+    uint32_t xe[4] = {1, (uint32_t)d.v, (uint32_t)d.u, 1};
+    gbconv_status_t s =
+        encode_tiled(&prm.tmX, in_t, 4, x, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_128B, xe);
     if (s != GBCONV_OK) return s;
     uint64_t wd[3] = {(uint64_t)d.C, (uint64_t)d.R * d.S, (uint64_t)d.K};
     uint64_t wstr[2] = {(uint64_t)d.C * eb, (uint64_t)d.R * d.S * d.C * eb};
@@ -521,14 +639,12 @@ gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, con
     prm.P = d.P;
     prm.Q = d.Q;
     prm.K = d.K;
-    prm.pw = d.pw;
-    prm.ph = d.ph;
-    prm.dh = d.dh;
-    prm.dw = d.dw;
-    prm.S = d.S;
+    prm.u = d.u;
     prm.RS = d.R * d.S;
     prm.wx_log2 = pl.wx_log2;
+    build_taps(d, pl.wx_log2, &prm);
     prm.TR = pl.TR;
+    prm.n_pos = pl.TR << pl.wx_log2;
     prm.c_blocks = pl.c_blocks;
     prm.k_tiles = (d.K + kt - 1) / kt;
     prm.p_tiles = (d.P + pl.TR - 1) / pl.TR;

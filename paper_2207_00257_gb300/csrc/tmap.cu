@@ -64,7 +64,8 @@ gbconv_status_t encode_im2col_act(CUtensorMap *m, const Dims &d, const void *x, 
 
 gbconv_status_t encode_tiled(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *ptr,
                              const uint64_t *dims, const uint64_t *strides_bytes,
-                             const uint32_t *box, CUtensorMapSwizzle swz) {
+                             const uint32_t *box, CUtensorMapSwizzle swz,
+                             const uint32_t *elem_strides) {
     std::call_once(g_once, load_entry_points);
     if (!g_tiled) return GBCONV_ERR_CUDA;
     if (reinterpret_cast<uintptr_t>(ptr) % 16) return GBCONV_ERR_ALIGNMENT;
@@ -74,7 +75,7 @@ gbconv_status_t encode_tiled(CUtensorMap *m, CUtensorMapDataType dt, int rank, c
     for (int i = 0; i < rank; ++i) {
         gd[i] = dims[i];
         bx[i] = box[i];
-        es[i] = 1;
+        es[i] = elem_strides ? elem_strides[i] : 1;
         if (i + 1 < rank) {
             gs[i] = strides_bytes[i];
             if (gs[i] % 16) return GBCONV_ERR_ALIGNMENT;

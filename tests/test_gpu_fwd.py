@@ -280,6 +280,15 @@ T_SHAPES = [  # the transposed band kernel: K <= 128, both output-channel tiles
     ConvShape(2, 32, 20, 30, 64, 3, 3, 1, 2, 2),      # dilation 2
     ConvShape(1, 64, 5, 120, 64, 3, 3, 1, 1, 1),      # Wx = 128, two rows per tile
     ConvShape(1, 64, 4, 150, 32, 1, 3, 1, (0, 1), 1),  # Wx = 256, one row per tile
+    # strided layers: taps grouped into phase images, one strided band per phase
+    ConvShape(2, 128, 17, 15, 128, 3, 3, 2, 1, 1),    # 4 phases (4, 2, 2, 1 taps), ragged
+    ConvShape(2, 64, 20, 22, 64, 3, 3, 2, 1, 1),
+    ConvShape(1, 64, 23, 19, 96, 5, 5, 2, 2, 1),      # shifts 0..2 in each phase
+    ConvShape(1, 32, 16, 40, 48, 3, 3, (2, 1), 1, 1),  # row stride only: 2 phases
+    ConvShape(1, 64, 22, 25, 64, 7, 7, 2, 3, 1),      # 7x7 stride 2, streamed filter
+    ConvShape(1, 64, 21, 21, 64, 3, 3, 2, 2, 2),      # stride 2, dilation 2: one phase
+    ConvShape(1, 64, 25, 25, 64, 3, 3, 3, 1, 1),      # stride 3: a phase per tap
+    ConvShape(1, 64, 9, 180, 64, 3, 3, 2, 1, 1),      # Wx = 128 at column stride 2
 ]
 
 
@@ -297,6 +306,20 @@ def test_bf16_transposed_band_kernel(sh, out):
     finally:
         B.gbconv_shutdown()
     assert r["err_i"] <= (TOL_ACC32 if out == "f32" else TOL_BF16_OUT), r["err_i"]
+
+
+@pytest.mark.parametrize("algo", [B.GBCONV_ALGO_IM2COL, B.GBCONV_ALGO_SHIFT_T])
+def test_fp8_strided_forward(algo):
+    sh = ConvShape(2, 256, 19, 17, 128, 3, 3, 2, 1, 1)
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                     B.GBCONV_E4M3, B.GBCONV_BF16, B.GBCONV_NHWC, B.GBCONV_FLAG_BIAS)
+    B.check(B.gbconv_set_config(B.GBCONV_OP_FWD, prob, B.gbconv_config_t(128, 0, 0, 0, algo)),
+            "set_config")
+    try:
+        r = fp8_case(sh, seed=73)
+    finally:
+        B.gbconv_shutdown()
+    assert r["err_i"] <= TOL_BF16_OUT and r["err_ii"] <= TOL_FP8, r
 
 
 @pytest.mark.parametrize("algo", [B.GBCONV_ALGO_IM2COL, B.GBCONV_ALGO_SHIFT])
