@@ -33,20 +33,22 @@
 //  * TMEM: two 256-column accumulators. For M = 128 row k of D^T sits in lane
 //    k; for M = 64 row k sits in lane 32*(k/16) + k%16 (lanes 16-31 of each
 //    quarter unused).
-//  * Epilogue: 8 warps, two groups of four (one warp per TMEM lane quarter).
-//    Group g takes 32-position chunks j = g, g+2, ... BF16 output: each warp
-//    reads its channels x 32 positions with 16x256b loads (the accumulator
-//    fragment layout: a thread holds two channels x two adjacent positions
-//    per 8-column group; for M = 64 the accumulator fills lanes 0-15 of each
-//    quarter), packs position pairs to bf16x2 and writes them with
-//    stmatrix.trans as position rows of 8 channels into a [32 positions][KT
-//    channels] tile in shared memory (128-byte swizzled rows). FP32 output:
-//    one channel row per thread (32x32b / 16x32bx2 loads), one 32-bit store
-//    per value. A named barrier joins the group, then one thread stores the
-//    tile with TMA through a 3-D map of y as [N*P][Q][K] (positions
-//    q >= Q and channels >= K clipped).
+//  * Epilogue: 16 warps, four groups of four (one warp per TMEM lane
+//    quarter). Group g takes 32-position chunks j = g, g+4, ...; every warp works on
+//    its own (channel quarter, chunk) with no barrier between warps. BF16
+//    output: 16x256b loads (the accumulator fragment layout: a thread holds
+//    two channels x two adjacent positions per 8-column group; for M = 64 the
+//    accumulator fills lanes 0-15 of each quarter), position pairs packed to
+//    bf16x2 and written with stmatrix.trans as position rows into the warp's
+//    own [32 positions][KT/4 channels] staging tile, read back as 16-byte
+//    units and stored to y with plain 16-byte stores (positions q >= Q and
+//    channels >= K skipped). FP32 output: one channel per thread
+//    (32x32b / 16x32bx2 loads), one 32-bit store per value; a warp's store
+//    covers consecutive channels of one position (two for M = 64).
 //
-// Warp roles and bounded waits as in tc_fwd.cu (320 threads).
+// Warp roles and bounded waits as in tc_fwd.cu (576 threads: the epilogue of
+// one chunk is a chain of dependent steps, so more warps in flight keep the
+// tail of a CTA's last tile short).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -60,8 +62,9 @@ namespace gbc {
 namespace {
 
 constexpr int NPOS = 256;  // accumulator columns per tile (largest MMA N)
-constexpr int NTHREADS = 320;
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;                 // four groups of four lane-quarter warps
+constexpr int EPI_GROUPS = EPI_WARPS / 4;
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;  // producer, MMA issuer, epilogue
 constexpr int SMEM_ALIGN = 1024;
 constexpr int BAR_BYTES = 512;
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -73,7 +76,6 @@ constexpr int MAX_TAPS = 128;
 struct TParams {
     CUtensorMap tmX;  // x [N][H][W][C], box {KE, v*Wx, u*nr, 1}, element strides {1, v, u, 1}
     CUtensorMap tmW;  // w [K][R*S][C], box {KE, 1, KT}
-    CUtensorMap tmY;  // y [N*P][Q][K], box {64 (BF16) | 32 (FP32), 32, 1}
     int N, P, Q, K;
     int u, RS;
     int wx_log2, TR, n_pos;  // n_pos = TR * Wx positions per tile (MMA N)
@@ -86,6 +88,7 @@ struct TParams {
     int band_bytes, band_stride, w_resident, stages_a, stages_b;
     int relu, out_f32;
     const float *bias, *x_scale, *w_scale;
+    void *y;  // [N][P][Q][K], BF16 or FP32
     Guard guard;
 };
 
@@ -98,18 +101,17 @@ __device__ __forceinline__ void tdecode(const TParams &p, int tile, int &n, int 
     p0 = (mt - n * p.p_tiles) * p.TR;
 }
 
-__device__ __forceinline__ void named_bar(int id, int count) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
 template <int KT, bool FP8>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_constant__ TParams prm) {
     constexpr int KE = FP8 ? 128 : 64;
     constexpr int TCOLS = 2 * NPOS;          // two 256-column accumulators
     constexpr int W_TILE = KT * 128;         // one filter tile (tap, channel block)
-    constexpr int STAGE_T = 32 * KT * 4;     // staging tile, worst case FP32: 32 x KT x 4 B
-    constexpr int EPI_TOTAL = 2 * 2 * STAGE_T;  // two groups x two buffers
     constexpr int KPW = KT / 4;              // output channels per warp (16 or 32)
+    constexpr int NH = KT / 64;              // 16-lane TMEM loads per chunk (BF16 output)
+    constexpr int UPR = KPW / 8;             // 16-byte units per staged position row (4 or 2)
+    constexpr int SWS = UPR == 4 ? 1 : 2;    // row shift of the staging swizzle
+    constexpr int WST = 32 * KPW * 2;        // per-warp staging tile: 32 positions x KPW bf16
+    constexpr int EPI_TOTAL = EPI_WARPS * WST;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -334,34 +336,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
         }
     } else {
         // ------------------------------ epilogue ------------------------------
-        const int ew = warp - 2;            // 0..7
+        const int ew = warp - 2;            // 0..EPI_WARPS-1
         const int quarter = warp & 3;       // TMEM lane quarter
-        const int group = ew >> 2;          // chunks j with j % 2 == group
-        // this thread's output-channel row within the tile (valid lanes only)
-        // KT = 128: lane = channel; KT = 64 (two-half loads): lanes l and l+16
-        // share channel l and split the chunk's positions
-        const int krow = quarter * KPW + (KT == 128 ? lane : (lane & 15));
-        constexpr int NH = KT / 64;              // 16-lane loads per chunk (BF16 output)
-        const int chb0 = quarter * KPW;          // first channel of this warp's lane quarter
-        uint8_t *gbuf = sEpi + group * 2 * STAGE_T;
-        int ebuf = 0;
+        const int group = ew >> 2;          // chunks j with j % EPI_GROUPS == group
+        const int chb0 = quarter * KPW;     // first channel of this warp's lane quarter
+        // FP32 output: this thread's channel. KT = 128: lane = channel; KT = 64
+        // (two-half loads): lanes l and l+16 share channel l and split the positions
+        const int krow = chb0 + (KT == 128 ? lane : (lane & 15));
+        uint8_t *wst = sEpi + ew * WST;     // this warp's staging tile
         const int wx_mask = (1 << prm.wx_log2) - 1;
         const float xs = FP8 ? __ldg(prm.x_scale) : 1.f;
+        const int nchunks = prm.n_pos >> 5;
         int local = 0;
         for (int tile = blockIdx.x; tile < prm.num_tiles; tile += gridDim.x, ++local) {
             int n, p0, kt;
             tdecode(prm, tile, n, p0, kt);
             const int acc = local & 1;
             const uint32_t aph = (local >> 1) & 1;
-            if (!ptx::mbar_wait(&tfull[acc], aph, lim, abort_flag)) {
-                fail();
-                break;
-            }
-            ptx::tc_fence_after();
-            // FP32 output: one channel row per thread (krow)
-            float scl = 1.f, bia = 0.f;
-            // BF16 output: 16-lane loads h, thread t holds channels chb(h) + t/4 + 8s
-            float bs[NH][2], ss[NH][2];
+            // per-channel constants, fetched before the accumulator is ready
+            float scl = 1.f, bia = 0.f;      // FP32 output: channel krow
+            float bs[NH][2], ss[NH][2];      // BF16 output: channels chb0 + 16h + 8s + lane/4
             if (prm.out_f32) {
                 const int k = kt * KT + krow;
                 if (k < prm.K) {
@@ -378,9 +372,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                         ss[h][s2] = (FP8 && k < prm.K) ? xs * __ldg(prm.w_scale + k) : 1.f;
                     }
             }
-            const int nchunks = prm.n_pos >> 5;
-            for (int j = group; j < nchunks; j += 2) {
-                uint32_t v[32];
+            if (!ptx::mbar_wait(&tfull[acc], aph, lim, abort_flag)) {
+                fail();
+                break;
+            }
+            ptx::tc_fence_after();
+            // TMEM load of chunk j into v (not waited for)
+            auto tload = [&](int j, uint32_t (&v)[32]) {
                 const uint32_t ta = tmem_base + ((uint32_t)(quarter * 32) << 16) +
                                     (uint32_t)(acc * NPOS + j * 32);
                 if (!prm.out_f32) {
@@ -393,85 +391,97 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                 } else {
                     ptx::tmem_ld_16x32bx2_x16(ta, *reinterpret_cast<uint32_t(*)[16]>(v));
                 }
-                ptx::tmem_ld_wait();
-                if (j + 2 >= nchunks) {
-                    ptx::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
-                }
+            };
+            // epilogue math and stores of chunk j from v
+            auto process = [&](int j, const uint32_t (&v)[32]) {
                 const int p = p0 + ((32 * j) >> prm.wx_log2);
                 const int q0 = (32 * j) & wx_mask;
-                const bool store = p < prm.P && q0 < prm.Q;
-                uint8_t *buf = gbuf + ebuf * STAGE_T;
-                if (store) {
-                    if (threadIdx.x == 64 + group * 128) ptx::bulk_wait_read<1>();
-                    named_bar(1 + group, 128);
-                    if (!prm.out_f32) {
-                        // Register 4g + 2s (+1) of load h: channel chb0 + 16h + 8s + t/4,
-                        // positions 8g + 2(t%4) (+1). Each packed pair is one row of an
-                        // 8x8 (channel x position) matrix; stmatrix.trans writes it as
-                        // 8 position rows of 8 channels (16 bytes) into the swizzled tile.
-                        const int mrow = lane & 7, msel = lane >> 3;
+                if (p >= prm.P || q0 >= prm.Q) return;
+                const size_t yrow = ((size_t)n * prm.P + p) * prm.Q + q0;  // y row of position q0
+                const int kw = kt * KT + chb0;                                // first channel of the warp
+                if (!prm.out_f32) {
+                    // Register 4g + 2s (+1) of load h: channel chb0 + 16h + 8s + t/4,
+                    // positions 8g + 2(t%4) (+1). Each packed pair is one row of an
+                    // 8x8 (channel x position) matrix; stmatrix.trans writes it as 8
+                    // position rows of 8 channels (16 bytes) into this warp's
+                    // [32 positions][KPW channels] tile. 16-byte units are swizzled
+                    // (unit c of row e at c ^ ((e >> SWS) & (UPR - 1))) so that the
+                    // eight rows of a matrix and the eight rows read back by a
+                    // quarter-warp fall in distinct bank groups.
+                    const int mrow = lane & 7, msel = lane >> 3;
+                    __syncwarp();  // previous chunk's reads of the tile are done
 #pragma unroll
-                        for (int h = 0; h < NH; ++h)
+                    for (int h = 0; h < NH; ++h)
 #pragma unroll
-                            for (int gp = 0; gp < 2; ++gp) {
-                                uint32_t pk[4];
+                        for (int gp = 0; gp < 2; ++gp) {
+                            uint32_t pk[4];
 #pragma unroll
-                                for (int m = 0; m < 4; ++m) {
-                                    const int g = 2 * gp + (m >> 1), s2 = m & 1;
-                                    float a0 = __uint_as_float(v[16 * h + 4 * g + 2 * s2]);
-                                    float a1 = __uint_as_float(v[16 * h + 4 * g + 2 * s2 + 1]);
-                                    if (FP8) {
-                                        a0 = a0 * ss[h][s2];
-                                        a1 = a1 * ss[h][s2];
-                                    }
-                                    a0 = a0 + bs[h][s2];
-                                    a1 = a1 + bs[h][s2];
-                                    if (prm.relu) {
-                                        a0 = fmaxf(a0, 0.f);
-                                        a1 = fmaxf(a1, 0.f);
-                                    }
-                                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(a0, a1);
-                                    pk[m] = *reinterpret_cast<const uint32_t *>(&b2);
+                            for (int m = 0; m < 4; ++m) {
+                                const int g = 2 * gp + (m >> 1), s2 = m & 1;
+                                float a0 = __uint_as_float(v[16 * h + 4 * g + 2 * s2]);
+                                float a1 = __uint_as_float(v[16 * h + 4 * g + 2 * s2 + 1]);
+                                if (FP8) {
+                                    a0 = a0 * ss[h][s2];
+                                    a1 = a1 * ss[h][s2];
                                 }
-                                const int e = 8 * (2 * gp + (msel >> 1)) + mrow;   // position
-                                const int ch = chb0 + 16 * h + 8 * (msel & 1);    // first channel
-                                const uint32_t addr = ptx::smem_addr(
-                                    buf + (ch >> 6) * 4096 + e * 128 + ((((ch & 63) >> 3) ^ (e & 7)) << 4));
-                                ptx::stmatrix_x4_trans(addr, pk[0], pk[1], pk[2], pk[3]);
+                                a0 = a0 + bs[h][s2];
+                                a1 = a1 + bs[h][s2];
+                                if (prm.relu) {
+                                    a0 = fmaxf(a0, 0.f);
+                                    a1 = fmaxf(a1, 0.f);
+                                }
+                                const __nv_bfloat162 b2 = __floats2bfloat162_rn(a0, a1);
+                                pk[m] = *reinterpret_cast<const uint32_t *>(&b2);
                             }
-                    } else {
-                        const int e0 = KT == 128 ? 0 : (lane >> 4) * 16;  // first position of this thread
-                        constexpr int NV = KT == 128 ? 32 : 16;
-                        const int qd = krow >> 5, kb = (krow & 31) * 4;
-                        uint8_t *hb = buf + qd * 4096 + (kb & 15);
+                            const int e = 8 * (2 * gp + (msel >> 1)) + mrow;  // position
+                            const int c = 2 * h + (msel & 1);                 // 16-byte unit
+                            ptx::stmatrix_x4_trans(
+                                ptx::smem_addr(wst + e * (UPR * 16) + ((c ^ ((e >> SWS) & (UPR - 1))) << 4)),
+                                pk[0], pk[1], pk[2], pk[3]);
+                        }
+                    __syncwarp();
+                    // read back 16-byte units (position e, unit c) and store them to y
+#pragma unroll
+                    for (int i = 0; i < UPR; ++i) {
+                        const int u = i * 32 + lane;
+                        const int e = u / UPR, c = u % UPR;
+                        const uint4 val = *reinterpret_cast<const uint4 *>(
+                            wst + e * (UPR * 16) + ((c ^ ((e >> SWS) & (UPR - 1))) << 4));
+                        const int k = kw + 8 * c;
+                        if (q0 + e < prm.Q && k < prm.K)
+                            *reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(prm.y) +
+                                                       (yrow + e) * prm.K + k) = val;
+                    }
+                } else {
+                    const int k = kt * KT + krow;
+                    const int e0 = KT == 128 ? 0 : (lane >> 4) * 16;  // first position of this thread
+                    constexpr int NV = KT == 128 ? 32 : 16;
+                    float *yf = static_cast<float *>(prm.y);
+                    if (k < prm.K) {
 #pragma unroll
                         for (int i = 0; i < NV; ++i) {
                             float a = __uint_as_float(v[i]);
                             if (FP8) a = a * scl;
                             a = a + bia;
                             if (prm.relu) a = fmaxf(a, 0.f);
-                            const int e = e0 + i;
-                            *reinterpret_cast<float *>(hb + e * 128 + (((kb >> 4) ^ (e & 7)) << 4)) = a;
+                            if (q0 + e0 + i < prm.Q) yf[(yrow + e0 + i) * prm.K + k] = a;
                         }
                     }
-                    ptx::fence_proxy_async_smem();
-                    named_bar(1 + group, 128);
-                    if (threadIdx.x == 64 + group * 128) {
-                        const int cols = prm.out_f32 ? 32 : 64;
-                        for (int h = 0; h < KT / cols; ++h) {
-                            const int kc = kt * KT + h * cols;
-                            if (kc < prm.K)
-                                ptx::tma_store_3d(&prm.tmY, buf + h * 4096, kc, q0, n * prm.P + p);
-                        }
-                        ptx::bulk_commit();
-                    }
-                    ebuf ^= 1;
                 }
+            };
+            for (int j = group; j < nchunks; j += EPI_GROUPS) {
+                uint32_t v[32];
+                tload(j, v);
+                ptx::tmem_ld_wait();
+                ptx::reg_fence(v);
+                if (j + EPI_GROUPS >= nchunks) {  // last TMEM read of this tile by this warp
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
+                }
+                process(j, v);
             }
         }
-        if (threadIdx.x == 64 + group * 128) ptx::bulk_wait<0>();
     }
 
     __syncwarp();
@@ -493,7 +503,7 @@ int ilog2(int v) {
 }
 
 template <int KT>
-constexpr int epi_total() { return 2 * 2 * 32 * KT * 4; }
+constexpr int epi_total() { return EPI_WARPS * 32 * (KT / 4) * 2; }  // per-warp staging tiles
 
 // Largest band shift of the phase decomposition: i = (r*dh) div u over the
 // rows, j = (s*dw) div v over the columns.
@@ -629,12 +639,8 @@ gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, con
     s = encode_tiled(&prm.tmW, in_t, 3, w, wd, wstr, wbx, CU_TENSOR_MAP_SWIZZLE_128B);
     if (s != GBCONV_OK) return s;
     const bool of32 = d.out_dtype == GBCONV_F32;
-    uint64_t yd[3] = {(uint64_t)d.K, (uint64_t)d.Q, (uint64_t)d.N * d.P};
-    uint64_t ys[2] = {(uint64_t)d.K * (of32 ? 4 : 2), (uint64_t)d.Q * d.K * (of32 ? 4 : 2)};
-    uint32_t yb[3] = {(uint32_t)(of32 ? 32 : 64), 32, 1};
-    s = encode_tiled(&prm.tmY, of32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                     3, y, yd, ys, yb, CU_TENSOR_MAP_SWIZZLE_128B);
-    if (s != GBCONV_OK) return s;
+    if (reinterpret_cast<uintptr_t>(y) % 16) return GBCONV_ERR_ALIGNMENT;  // 16-byte stores
+    prm.y = y;
     prm.N = d.N;
     prm.P = d.P;
     prm.Q = d.Q;
