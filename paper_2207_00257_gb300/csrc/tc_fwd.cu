@@ -154,6 +154,14 @@ __global__ void __launch_bounds__(EpiShape<BN>::threads, 1) tc_fwd_kernel(const 
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // Tensor-map descriptors do not depend on earlier kernels: fetch them
+    // while the previous kernel drains.
+    if (warp == 0)
+        for (int g = lane; g < prm.count; g += 32) {
+            ptx::prefetch_tmap(&prm.tmA[g]);
+            ptx::prefetch_tmap(&prm.tmB[g]);
+            ptx::prefetch_tmap(&prm.tmY[g]);
+        }
     // Prologue done: now wait for the kernels this one depends on, and let the
     // next kernel on the stream start launching.
     ptx::griddep_wait();

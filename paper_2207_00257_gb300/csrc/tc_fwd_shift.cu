@@ -133,6 +133,11 @@ __global__ void __launch_bounds__(EpiShape<BN>::threads, 1)
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    if (threadIdx.x == 0) {  // descriptors do not depend on earlier kernels
+        ptx::prefetch_tmap(&prm.tmX);
+        ptx::prefetch_tmap(&prm.tmB);
+        ptx::prefetch_tmap(&prm.tmY);
+    }
     // Prologue done: now wait for the kernels this one depends on, and let the
     // next kernel on the stream start launching.
     ptx::griddep_wait();

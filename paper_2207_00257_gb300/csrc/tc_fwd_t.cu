@@ -26,8 +26,10 @@
 //    positions (Wx = power of two >= Q + max j; TR <= 256 / Wx, chosen to
 //    split the P rows into equal tiles), times KT output channels.
 //  * A operand: filter tile W[(r,s), c block] = KT rows of 128 bytes, resident
-//    in shared memory when the whole filter fits, otherwise streamed in
-//    table order.
+//    in shared memory when the whole filter fits (loaded during the first
+//    tile, each phase's tiles right behind its band, with barriers per group
+//    of tiles so the first MMAs do not wait for the whole filter), otherwise
+//    streamed in table order.
 //  * B operand: 256 band rows starting at the tap's shift (K-major, 128-byte
 //    swizzle; any 128-byte row is a valid start).
 //  * TMEM: two 256-column accumulators. For M = 128 row k of D^T sits in lane
@@ -66,9 +68,10 @@ constexpr int EPI_WARPS = 16;                 // four groups of four lane-quarte
 constexpr int EPI_GROUPS = EPI_WARPS / 4;
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;  // producer, MMA issuer, epilogue
 constexpr int SMEM_ALIGN = 1024;
-constexpr int BAR_BYTES = 512;
+constexpr int BAR_BYTES = 1024;
 constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr int MAX_SA = 4, MAX_SB = 12;
+constexpr int MAX_WRES = 32;  // barriers over the tiles of a resident filter
 constexpr int MAX_STRIDE = 4;
 constexpr int MAX_PHASES = MAX_STRIDE * MAX_STRIDE;
 constexpr int MAX_TAPS = 128;
@@ -79,6 +82,8 @@ struct TParams {
     int N, P, Q, K;
     int u, RS;
     int wx_log2, TR, n_pos;  // n_pos = TR * Wx positions per tile (MMA N)
+    int flat;                // 1x1 stride-1 unpadded: x and y as [N*H*W] rows, tiles of n_pos rows
+    int M;                   // flat: N*H*W
     // phase f: band origin (column b - pw, row offset a - ph), taps [end[f-1], end[f])
     int n_phase;
     int ph_w0[MAX_PHASES], ph_h0[MAX_PHASES], ph_end[MAX_PHASES];
@@ -94,9 +99,16 @@ struct TParams {
 
 static_assert(sizeof(TParams) <= 4096, "transposed kernel parameters too large");
 
+// Tile -> (image n, first output row p0, output-channel tile kt); flat
+// layers: n = 0 and p0 = first position row of the tile.
 __device__ __forceinline__ void tdecode(const TParams &p, int tile, int &n, int &p0, int &kt) {
     kt = tile % p.k_tiles;
     const int mt = tile / p.k_tiles;
+    if (p.flat) {
+        n = 0;
+        p0 = mt * p.n_pos;
+        return;
+    }
     n = mt / p.p_tiles;
     p0 = (mt - n * p.p_tiles) * p.TR;
 }
@@ -129,7 +141,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
     uint64_t *tfull = emptyW + MAX_SB;
     uint64_t *tempty = tfull + 2;
     uint64_t *done = tempty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    // Resident filter: tiles stored in the order the MMAs use them (channel
+    // block, then tap-table entry), consecutive tiles grouped `wper` to a
+    // barrier, so the first MMAs need only the first tiles.
+    uint64_t *wres = done + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wres + MAX_WRES);
+    const int w_tiles = prm.RS * prm.c_blocks;
+    const int wper = (w_tiles + MAX_WRES - 1) / MAX_WRES;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -140,9 +158,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
             ptx::mbar_init(&fullA[i], 1);
             ptx::mbar_init(&emptyA[i], 1);
         }
-        for (int i = 0; i < (prm.w_resident ? 1 : SB); ++i) {
-            ptx::mbar_init(&fullW[i], 1);
-            ptx::mbar_init(&emptyW[i], 1);
+        if (prm.w_resident) {
+            for (int i = 0; i * wper < w_tiles; ++i) ptx::mbar_init(&wres[i], 1);
+        } else {
+            for (int i = 0; i < SB; ++i) {
+                ptx::mbar_init(&fullW[i], 1);
+                ptx::mbar_init(&emptyW[i], 1);
+            }
         }
         for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(&tfull[i], 1);
@@ -160,6 +182,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    if (threadIdx.x == 0) {  // descriptors do not depend on earlier kernels
+        ptx::prefetch_tmap(&prm.tmX);
+        ptx::prefetch_tmap(&prm.tmW);
+    }
     ptx::griddep_wait();
     if (threadIdx.x == 0) ptx::griddep_launch();
 
@@ -173,17 +199,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
             // ------------------------------ producer ------------------------------
             const bool skip = prm.guard.skip_loads != 0;
             bool ok = true;
-            int issued_w = 0;
-            if (prm.w_resident && !skip) {
-                // resident filter: every (channel block, tap) tile of output-channel tile 0
-                // (a resident filter implies a single output-channel tile)
-                ptx::mbar_arrive_expect_tx(&fullW[0], (uint32_t)(prm.RS * prm.c_blocks * W_TILE));
-                for (int cb = 0; cb < prm.c_blocks; ++cb)
-                    for (int t = 0; t < prm.RS; ++t)
-                        ptx::tma_load_3d(sW + (cb * prm.RS + t) * W_TILE, &prm.tmW, &fullW[0],
-                                         cb * KE, t, 0);
-                issued_w = 1;
-            }
+            int issued_w = 0;  // resident filter tiles issued (during the first tile)
             int sa = 0, sb = 0;
             uint32_t pa = 0, pb = 0;
             int issued_a = 0, issued_b = 0;
@@ -199,15 +215,32 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                         }
                         if (!skip) {
                             ptx::mbar_arrive_expect_tx(&fullA[sa], (uint32_t)prm.band_bytes);
-                            ptx::tma_load_4d(sA + sa * prm.band_stride, &prm.tmX, &fullA[sa], cb * KE,
-                                             prm.ph_w0[f], prm.u * p0 + prm.ph_h0[f], n);
+                            if (prm.flat)
+                                ptx::tma_load_2d(sA + sa * prm.band_stride, &prm.tmX, &fullA[sa],
+                                                 cb * KE, p0);
+                            else
+                                ptx::tma_load_4d(sA + sa * prm.band_stride, &prm.tmX, &fullA[sa],
+                                                 cb * KE, prm.ph_w0[f], prm.u * p0 + prm.ph_h0[f], n);
                             ++issued_a;
                         }
                         if (++sa == SA) {
                             sa = 0;
                             pa ^= 1;
                         }
-                        if (prm.w_resident) continue;
+                        if (prm.w_resident) {
+                            // first tile: this phase's filter tiles, right behind its band
+                            if (skip || issued_w == w_tiles) continue;
+                            for (int ti = f ? prm.ph_end[f - 1] : 0; ti < prm.ph_end[f]; ++ti) {
+                                const int seq = cb * prm.RS + ti, b = seq / wper;
+                                if (seq % wper == 0)
+                                    ptx::mbar_arrive_expect_tx(
+                                        &wres[b], (uint32_t)(min(wper, w_tiles - b * wper) * W_TILE));
+                                ptx::tma_load_3d(sW + seq * W_TILE, &prm.tmW, &wres[b], cb * KE,
+                                                 prm.tap_t[ti], 0);
+                                ++issued_w;
+                            }
+                            continue;
+                        }
                         for (int ti = f ? prm.ph_end[f - 1] : 0; ti < prm.ph_end[f]; ++ti) {
                             if (!ptx::mbar_wait(&emptyW[sb], pb ^ 1, lim, abort_flag)) {
                                 fail();
@@ -253,16 +286,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                     if (!ptx::mbar_wait(&fullW[st], ph, lim, &zero)) fail();
                 }
             }
-            if (issued_w && !ptx::mbar_wait(&fullW[0], 0, lim, &zero)) fail();
+            // resident filter groups fully issued (a group is complete only when all its tiles were)
+            for (int b = 0; b * wper < issued_w; ++b)
+                if (!ptx::mbar_wait(&wres[b], 0, lim, &zero)) fail();
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------ MMA issuer ----------------------------
             bool ok = true;
-            if (prm.w_resident && !ptx::mbar_wait(&fullW[0], 0, lim, abort_flag)) {
-                fail();
-                ok = false;
-            }
             uint32_t idesc = FP8 ? ptx::idesc_e4m3(prm.n_pos) : ptx::idesc_bf16(prm.n_pos);
             idesc = (idesc & ~(0x1Fu << 24)) | ((uint32_t)(KT >> 4) << 24);  // M = KT
             int sa = 0, sb = 0;
@@ -290,7 +321,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                         for (int ti = f ? prm.ph_end[f - 1] : 0; ti < prm.ph_end[f]; ++ti) {
                             uint32_t w_addr;
                             if (prm.w_resident) {
-                                w_addr = ptx::smem_addr(sW + (cb * prm.RS + prm.tap_t[ti]) * W_TILE);
+                                const int seq = cb * prm.RS + ti;
+                                if (local == 0) {  // first tile: wait for this tile's group
+                                    if (!ptx::mbar_wait(&wres[seq / wper], 0, lim, abort_flag)) {
+                                        fail();
+                                        ok = false;
+                                        break;
+                                    }
+                                    ptx::tc_fence_after();
+                                }
+                                w_addr = ptx::smem_addr(sW + seq * W_TILE);
                             } else {
                                 if (!ptx::mbar_wait(&fullW[sb], pb, lim, abort_flag)) {
                                     fail();
@@ -394,10 +434,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
             };
             // epilogue math and stores of chunk j from v
             auto process = [&](int j, const uint32_t (&v)[32]) {
-                const int p = p0 + ((32 * j) >> prm.wx_log2);
-                const int q0 = (32 * j) & wx_mask;
-                if (p >= prm.P || q0 >= prm.Q) return;
-                const size_t yrow = ((size_t)n * prm.P + p) * prm.Q + q0;  // y row of position q0
+                size_t yrow;  // y row of the chunk's first position
+                int nvalid;   // positions of the chunk inside y
+                if (prm.flat) {
+                    const int m0 = p0 + 32 * j;
+                    if (m0 >= prm.M) return;
+                    yrow = (size_t)m0;
+                    nvalid = prm.M - m0;
+                } else {
+                    const int p = p0 + ((32 * j) >> prm.wx_log2);
+                    const int q0 = (32 * j) & wx_mask;
+                    if (p >= prm.P || q0 >= prm.Q) return;
+                    yrow = ((size_t)n * prm.P + p) * prm.Q + q0;
+                    nvalid = prm.Q - q0;
+                }
                 const int kw = kt * KT + chb0;                                // first channel of the warp
                 if (!prm.out_f32) {
                     // Register 4g + 2s (+1) of load h: channel chb0 + 16h + 8s + t/4,
@@ -448,7 +498,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                         const uint4 val = *reinterpret_cast<const uint4 *>(
                             wst + e * (UPR * 16) + ((c ^ ((e >> SWS) & (UPR - 1))) << 4));
                         const int k = kw + 8 * c;
-                        if (q0 + e < prm.Q && k < prm.K)
+                        if (e < nvalid && k < prm.K)
                             *reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(prm.y) +
                                                        (yrow + e) * prm.K + k) = val;
                     }
@@ -464,7 +514,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                             if (FP8) a = a * scl;
                             a = a + bia;
                             if (prm.relu) a = fmaxf(a, 0.f);
-                            if (q0 + e0 + i < prm.Q) yf[(yrow + e0 + i) * prm.K + k] = a;
+                            if (e0 + i < nvalid) yf[(yrow + e0 + i) * prm.K + k] = a;
                         }
                     }
                 }
@@ -494,7 +544,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
 struct TPlan {
     int wx_log2, TR, nr, band_bytes, band_stride, c_blocks, w_resident, stages_a, stages_b;
     int n_phase;
+    int flat, n_pos, k_tiles;
+    long long num_tiles;
 };
+
+// A 1x1, stride-1, unpadded layer is a plain GEMM over the N*H*W positions.
+bool is_flat(const Dims &d) {
+    return d.R == 1 && d.S == 1 && d.u == 1 && d.v == 1 && d.ph == 0 && d.pw == 0;
+}
 
 int ilog2(int v) {
     int l = 0;
@@ -527,29 +584,57 @@ bool make_plan(const Dims &d, int kt, TPlan *pl) {
     if (d.u > MAX_STRIDE || d.v > MAX_STRIDE || d.R * d.S > MAX_TAPS) return false;
     const bool fp8 = d.in_dtype == GBCONV_E4M3;
     const int ke = fp8 ? 128 : 64;
-    const int imax = max_shift(d.R, d.dh, d.u), jmax = max_shift(d.S, d.dw, d.v);
-    const int need = d.Q + jmax;
-    int wx = 32;
-    while (wx < need) wx *= 2;
-    if (wx > NPOS || wx * d.v > 256) return false;  // TMA box extent <= 256
+    const int k_tiles = (d.K + kt - 1) / kt;
     TPlan p{};
-    p.wx_log2 = ilog2(wx);
-    // rows per tile: at most 256 / Wx, spread evenly over the output rows
-    const int tr_max = NPOS / wx;
-    const int row_tiles = std::max(1, (d.P + tr_max - 1) / tr_max);
-    p.TR = std::max(1, (d.P + row_tiles - 1) / row_tiles);
-    p.nr = p.TR + imax;
-    if (p.nr * d.u > 256) return false;
-    p.band_bytes = 128 * wx * p.nr;
-    p.band_stride = (p.band_bytes + jmax * 128 + 1023) / 1024 * 1024;
-    if (p.band_stride > 80 * 1024) return false;
+    p.k_tiles = k_tiles;
     p.c_blocks = (d.C + ke - 1) / ke;
-    p.n_phase = count_phases(d);
+    if (is_flat(d)) {
+        // Tiles of n_pos consecutive positions; n_pos (a multiple of 32, 128..256)
+        // minimises the rounds of tiles over the SMs, each round costing its
+        // positions plus about 32 positions' worth of per-tile overhead.
+        const long long M = d.M();
+        const int sms = sm_count();
+        long long best = -1;
+        for (int np = 256; np >= 128; np -= 32) {
+            const long long tiles = (M + np - 1) / np * k_tiles;
+            const long long cost = (tiles + sms - 1) / sms * (np + 32);
+            if (best < 0 || cost < best) {
+                best = cost;
+                p.n_pos = np;
+            }
+        }
+        p.flat = 1;
+        p.wx_log2 = 0;
+        p.TR = 1;
+        p.nr = 1;
+        p.n_phase = 1;
+        p.num_tiles = (M + p.n_pos - 1) / p.n_pos * k_tiles;
+        p.band_bytes = 128 * p.n_pos;
+        p.band_stride = (p.band_bytes + 1023) / 1024 * 1024;
+    } else {
+        const int imax = max_shift(d.R, d.dh, d.u), jmax = max_shift(d.S, d.dw, d.v);
+        const int need = d.Q + jmax;
+        int wx = 32;
+        while (wx < need) wx *= 2;
+        if (wx > NPOS || wx * d.v > 256) return false;  // TMA box extent <= 256
+        p.wx_log2 = ilog2(wx);
+        // rows per tile: at most 256 / Wx, spread evenly over the output rows
+        const int tr_max = NPOS / wx;
+        const int row_tiles = std::max(1, (d.P + tr_max - 1) / tr_max);
+        p.TR = std::max(1, (d.P + row_tiles - 1) / row_tiles);
+        p.nr = p.TR + imax;
+        if (p.nr * d.u > 256) return false;
+        p.band_bytes = 128 * wx * p.nr;
+        p.band_stride = (p.band_bytes + jmax * 128 + 1023) / 1024 * 1024;
+        if (p.band_stride > 80 * 1024) return false;
+        p.n_phase = count_phases(d);
+        p.num_tiles = (long long)d.N * ((d.P + p.TR - 1) / p.TR) * k_tiles;
+        p.n_pos = p.TR << p.wx_log2;
+    }
     const int epi = kt == 128 ? epi_total<128>() : epi_total<64>();
     const int budget = SMEM_LIMIT - SMEM_ALIGN - BAR_BYTES - epi;
     const int wtile = kt * 128;
     const long long w_total = (long long)d.R * d.S * p.c_blocks * wtile;
-    const int k_tiles = (d.K + kt - 1) / kt;
     if (k_tiles == 1 && w_total + 2ll * p.band_stride <= budget) {
         p.w_resident = 1;
         p.stages_a = (int)std::min<long long>(MAX_SA, (budget - w_total) / p.band_stride);
@@ -606,7 +691,8 @@ gbconv_status_t launch(const TParams &prm, size_t smem, int grid, cudaStream_t s
 
 // Output-channel tile of the transposed kernel for this layer (0 if none fits).
 int tc_fwd_t_tile(const Dims &d) {
-    if (!tc_fwd_supported(d) || d.K > 128) return 0;
+    if (!tc_fwd_supported(d)) return 0;
+    if (d.K > 128 && !is_flat(d)) return 0;  // a band would be fetched once per channel tile
     const int kt = d.K <= 64 ? 64 : 128;
     TPlan p;
     return make_plan(d, kt, &p) ? kt : 0;
@@ -626,12 +712,20 @@ gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, con
         fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     TParams prm;
     memset(&prm, 0, sizeof(prm));
-    uint64_t xd[4] = {(uint64_t)d.C, (uint64_t)d.W, (uint64_t)d.H, (uint64_t)d.N};
-    uint64_t xs[3] = {(uint64_t)d.C * eb, (uint64_t)d.W * d.C * eb, (uint64_t)d.H * d.W * d.C * eb};
-    uint32_t xb[4] = {(uint32_t)ke, (uint32_t)(d.v << pl.wx_log2), (uint32_t)(d.u * pl.nr), 1};
-    uint32_t xe[4] = {1, (uint32_t)d.v, (uint32_t)d.u, 1};
-    gbconv_status_t s =
-        encode_tiled(&prm.tmX, in_t, 4, x, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_128B, xe);
+    gbconv_status_t s;
+    if (pl.flat) {  // x as [N*H*W][C], boxes of n_pos rows
+        uint64_t xd[2] = {(uint64_t)d.C, (uint64_t)d.M()};
+        uint64_t xs[1] = {(uint64_t)d.C * eb};
+        uint32_t xb[2] = {(uint32_t)ke, (uint32_t)pl.n_pos};
+        s = encode_tiled(&prm.tmX, in_t, 2, x, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_128B);
+    } else {
+        uint64_t xd[4] = {(uint64_t)d.C, (uint64_t)d.W, (uint64_t)d.H, (uint64_t)d.N};
+        uint64_t xs[3] = {(uint64_t)d.C * eb, (uint64_t)d.W * d.C * eb,
+                          (uint64_t)d.H * d.W * d.C * eb};
+        uint32_t xb[4] = {(uint32_t)ke, (uint32_t)(d.v << pl.wx_log2), (uint32_t)(d.u * pl.nr), 1};
+        uint32_t xe[4] = {1, (uint32_t)d.v, (uint32_t)d.u, 1};
+        s = encode_tiled(&prm.tmX, in_t, 4, x, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_128B, xe);
+    }
     if (s != GBCONV_OK) return s;
     uint64_t wd[3] = {(uint64_t)d.C, (uint64_t)d.R * d.S, (uint64_t)d.K};
     uint64_t wstr[2] = {(uint64_t)d.C * eb, (uint64_t)d.R * d.S * d.C * eb};
@@ -650,13 +744,14 @@ gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, con
     prm.wx_log2 = pl.wx_log2;
     build_taps(d, pl.wx_log2, &prm);
     prm.TR = pl.TR;
-    prm.n_pos = pl.TR << pl.wx_log2;
+    prm.n_pos = pl.n_pos;
+    prm.flat = pl.flat;
+    prm.M = (int)d.M();
     prm.c_blocks = pl.c_blocks;
-    prm.k_tiles = (d.K + kt - 1) / kt;
+    prm.k_tiles = pl.k_tiles;
     prm.p_tiles = (d.P + pl.TR - 1) / pl.TR;
-    const long long tiles = (long long)d.N * prm.p_tiles * prm.k_tiles;
-    if (tiles >= (1ll << 31)) return GBCONV_ERR_UNSUPPORTED;
-    prm.num_tiles = (int)tiles;
+    if (pl.num_tiles >= (1ll << 31)) return GBCONV_ERR_UNSUPPORTED;
+    prm.num_tiles = (int)pl.num_tiles;
     prm.band_bytes = pl.band_bytes;
     prm.band_stride = pl.band_stride;
     prm.w_resident = pl.w_resident;

@@ -289,6 +289,10 @@ T_SHAPES = [  # the transposed band kernel: K <= 128, both output-channel tiles
     ConvShape(1, 64, 21, 21, 64, 3, 3, 2, 2, 2),      # stride 2, dilation 2: one phase
     ConvShape(1, 64, 25, 25, 64, 3, 3, 3, 1, 1),      # stride 3: a phase per tap
     ConvShape(1, 64, 9, 180, 64, 3, 3, 2, 1, 1),      # Wx = 128 at column stride 2
+    # 1x1 stride-1 layers: flat GEMM over N*H*W positions, ragged last tile
+    ConvShape(3, 64, 7, 9, 64, 1, 1, 1, 0, 1),        # 189 positions: one partial tile
+    ConvShape(2, 128, 15, 17, 256, 1, 1, 1, 0, 1),    # 256 channels: two channel tiles
+    ConvShape(1, 256, 20, 21, 96, 1, 1, 1, 0, 1),     # four channel blocks, K on a 128 tile
 ]
 
 
@@ -309,8 +313,9 @@ def test_bf16_transposed_band_kernel(sh, out):
 
 
 @pytest.mark.parametrize("algo", [B.GBCONV_ALGO_IM2COL, B.GBCONV_ALGO_SHIFT_T])
-def test_fp8_strided_forward(algo):
-    sh = ConvShape(2, 256, 19, 17, 128, 3, 3, 2, 1, 1)
+@pytest.mark.parametrize("sh", [ConvShape(2, 256, 19, 17, 128, 3, 3, 2, 1, 1),
+                                ConvShape(2, 256, 13, 19, 192, 1, 1, 1, 0, 1)], ids=_id)
+def test_fp8_strided_and_flat_forward(algo, sh):
     prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
                      B.GBCONV_E4M3, B.GBCONV_BF16, B.GBCONV_NHWC, B.GBCONV_FLAG_BIAS)
     B.check(B.gbconv_set_config(B.GBCONV_OP_FWD, prob, B.gbconv_config_t(128, 0, 0, 0, algo)),
