@@ -562,14 +562,42 @@ def bench_backward(torch, dev, args, dist_on, pk):
         def __init__(s, f):
             s.launch = f
 
+    # data gradient of the strided ResNet layer (3x3 stride 2, 128 -> 128, 56 -> 28):
+    # sub-pixel phases on the tensor cores, and the CUDA-core gather kernel
+    # (which the allocation-free entry point uses for strided layers)
+    from paper_2207_00257_gb300.synth import resnet_layers
+    s2 = resnet_layers(32)[3]
+    _, w2, _, g2 = make_inputs(s2, 6, grad=True)
+    w2b, g2b = w2.bfloat16().to(dev), g2.bfloat16().to(dev)
+    dx2 = torch.empty(s2.x_shape(), dtype=torch.bfloat16, device=dev)
+    prob2 = B.problem(s2.N, s2.C, s2.H, s2.W, s2.K, s2.R, s2.S, s2.stride, s2.pad, s2.dil,
+                      B.GBCONV_BF16, B.GBCONV_BF16, B.GBCONV_NHWC, 0)
+    _, nd2 = B.gbconv_workspace_size(B.GBCONV_OP_DGRAD, prob2)
+    wsd2 = torch.empty(max(nd2, 1), dtype=torch.uint8, device=dev)
+
+    def dgrad_s2(i, stream):
+        B.check(B.conv2d_dgrad(prob2, g2b.data_ptr(), w2b.data_ptr(), dx2.data_ptr(),
+                               wsd2.data_ptr(), nd2, stream), "dgrad s2")
+
+    def dgrad_s2_cuda_cores(i, stream):
+        B.check(B.conv2d_dgrad_noalloc(prob2, g2b.data_ptr(), w2b.data_ptr(), dx2.data_ptr(),
+                                       stream), "dgrad s2 (CUDA cores)")
+
     steps = max(3, min(args.steps, 20))
-    res = bench_layers([L(dgrad), L(wgrad)], steps, 3, 1, torch, dist_on)
+    res = bench_layers([L(dgrad), L(wgrad), L(dgrad_s2), L(dgrad_s2_cuda_cores)], steps, 3, 1,
+                       torch, dist_on)
     f = sh.flops
+    f2 = s2.flops
     return {"workload": sh.tag, "dgrad_us": round(res["launch_us"][0], 1),
             "wgrad_us": round(res["launch_us"][1], 1),
             "dgrad_tflops": round(f / (res["launch_us"][0] * 1e-6) / 1e12, 1),
             "wgrad_tflops": round(f / (res["launch_us"][1] * 1e-6) / 1e12, 1),
-            "wgrad_split_k": B.gbconv_get_config(B.GBCONV_OP_WGRAD, prob)[1].split_k}
+            "wgrad_split_k": B.gbconv_get_config(B.GBCONV_OP_WGRAD, prob)[1].split_k,
+            "dgrad_stride2": {"workload": "dgrad_" + s2.tag,
+                              "subpixel_tc_us": round(res["launch_us"][2], 1),
+                              "subpixel_tc_tflops": round(f2 / (res["launch_us"][2] * 1e-6) / 1e12, 1),
+                              "cuda_core_us": round(res["launch_us"][3], 1),
+                              "cuda_core_tflops": round(f2 / (res["launch_us"][3] * 1e-6) / 1e12, 2)}}
 
 
 # ---------------------------------------------------------------------------

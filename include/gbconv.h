@@ -138,8 +138,14 @@ gbconv_status_t conv2d_fwd(const gbconv_problem_t *prob, const void *x, const vo
  *   dy [N,P,Q,K] or [N,K,P,Q] (in_dtype), w as in conv2d_fwd (in_dtype),
  *   dx [N,H,W,C] or [N,C,H,W] (out_dtype). dx is fully overwritten.
  * BF16 NHWC with stride 1 and pad <= dil*(R-1) runs on the tensor cores as a
- * forward convolution of dy with the rotated filter (needs the workspace);
- * everything else runs on a CUDA-core gather kernel with FP32 accumulation. */
+ * forward convolution of dy with the rotated filter. Other BF16 NHWC layers
+ * (strides up to 4, any padding, channels multiples of 8) run on the tensor
+ * cores by sub-pixel phases: for each output phase (h mod u, w mod v) the
+ * taps that reach it form a stride-1 correlation of dy with the transposed
+ * filter, written to every u-th row and v-th column of dx; phases no tap
+ * reaches are zeroed. Both tensor-core forms need the workspace (the filter,
+ * rotated or transposed: K*R*S*C*2 bytes, see gbconv_workspace_size).
+ * Everything else runs on a CUDA-core gather kernel with FP32 accumulation. */
 gbconv_status_t conv2d_dgrad(const gbconv_problem_t *prob, const void *dy, const void *w,
                              void *dx, void *ws, size_t ws_bytes, gbconv_stream_t stream);
 
@@ -225,7 +231,9 @@ gbconv_status_t gbconv_debug_set(int32_t key, int64_t value);
  * GBCONV_DGRAD_STATIC_SCRATCH_BYTES bytes that the library holds on every GPU
  * that loads it, until the process exits. Filters whose K*R*S*C*2 bytes exceed
  * that size are refused with GBCONV_ERR_WORKSPACE before anything is enqueued.
- * Problems conv2d_dgrad runs on the CUDA-core kernel need no scratch at all.
+ * Every other problem (including the strided layers that conv2d_dgrad runs
+ * as sub-pixel phases) runs here on the CUDA-core kernel and needs no
+ * scratch at all.
  *
  * The first call on each device looks up the array's device address (a CUDA
  * runtime query, done once per device with that device current); make that

@@ -226,6 +226,16 @@ gbconv_status_t do_dgrad(const Dims &d, const TcConfig &cfg, const void *dy, con
         if (s != GBCONV_OK) return s;
         return launch_tc_fwd(t, cfg, dy, ws, nullptr, nullptr, nullptr, dx, st);
     }
+    if (tc_dgrad_t_supported(d)) {
+        // strided (or over-padded) layer: sub-pixel phases on tensor cores with
+        // the transposed filter in the workspace
+        size_t need = round256((size_t)d.K * d.R * d.S * d.C * 2);
+        if (!ws || ws_bytes < need) return GBCONV_ERR_WORKSPACE;
+        if (!aligned16(ws) || !aligned16(dy) || !aligned16(dx)) return GBCONV_ERR_ALIGNMENT;
+        gbconv_status_t s = launch_transpose_filter(d, w, ws, st);
+        if (s != GBCONV_OK) return s;
+        return launch_tc_dgrad_t(d, dy, ws, dx, st);
+    }
     return launch_simt_dgrad(d, dy, w, dx, st);
 }
 
@@ -304,7 +314,8 @@ gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, 
     if (op == GBCONV_OP_FWD) return GBCONV_OK;
     if (op == GBCONV_OP_DGRAD) {
         Dims t;
-        if (dgrad_as_fwd(d, &t)) *bytes = round256((size_t)d.K * d.R * d.S * d.C * 2);
+        if (dgrad_as_fwd(d, &t) || tc_dgrad_t_supported(d))
+            *bytes = round256((size_t)d.K * d.R * d.S * d.C * 2);
         return GBCONV_OK;
     }
     if (op == GBCONV_OP_WGRAD) {

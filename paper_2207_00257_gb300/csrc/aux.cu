@@ -124,6 +124,45 @@ __global__ void rotate_krsc(const T *__restrict__ w, T *__restrict__ wr, int K, 
     }
 }
 
+// Filter transpose w[k][r][s][c] -> wT[c][r][s][k] (no rotation): the filter
+// of the sub-pixel data-gradient phases.
+template <typename T>
+__global__ void transpose_krsc(const T *__restrict__ w, T *__restrict__ wt, int K, int RS, int C) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
+    long long total = (long long)K * RS * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        // i indexes the output [c][t][k]
+        int k = (int)(i % K);
+        long long t = i / K;
+        int rs = (int)(t % RS);
+        int c = (int)(t / RS);
+        wt[i] = w[((long long)k * RS + rs) * C + c];
+    }
+}
+
+// Zeroes the positions (n, u*h' + a, v*w' + b, :) of an NHWC tensor: a
+// sub-pixel phase of the data gradient that no filter tap reaches.
+template <typename T>
+__global__ void zero_phase(T *__restrict__ dx, int N, int H, int W, int C, int u, int v, int a,
+                           int b) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
+    const int Ha = (H - a + u - 1) / u, Wb = (W - b + v - 1) / v;
+    const long long total = (long long)N * Ha * Wb * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long t = i / C;
+        const int wq = (int)(t % Wb);
+        t /= Wb;
+        const int hq = (int)(t % Ha);
+        const int n = (int)(t / Ha);
+        dx[(((long long)n * H + (long long)hq * u + a) * W + (long long)wq * v + b) * C + c] = T(0.f);
+    }
+}
+
 // Vector of 8 consecutive input values as float (16 B of BF16, or two 16-B
 // loads of FP32). The caller guarantees alignment and bounds.
 __device__ __forceinline__ void load8(const float *p, float (&v)[8]) {
@@ -273,6 +312,30 @@ gbconv_status_t launch_rotate_filter(const Dims &d, const void *w, void *w_rot, 
                        (float *)w_rot, d.K, d.R, d.S, d.C);
     else
         return GBCONV_ERR_UNSUPPORTED;
+    return cuda_status(e);
+}
+
+gbconv_status_t launch_transpose_filter(const Dims &d, const void *w, void *wt, cudaStream_t st) {
+    long long total = (long long)d.K * d.R * d.S * d.C;
+    unsigned g = grid_for(total, 256);
+    if (d.in_dtype != GBCONV_BF16) return GBCONV_ERR_UNSUPPORTED;
+    return cuda_status(launch_pdl(transpose_krsc<__nv_bfloat16>, dim3(g), dim3(256), 0, st,
+                                  (const __nv_bfloat16 *)w, (__nv_bfloat16 *)wt, d.K, d.R * d.S,
+                                  d.C));
+}
+
+gbconv_status_t launch_zero_phase(const Dims &d, void *dx, int a, int b, cudaStream_t st) {
+    const int Ha = (d.H - a + d.u - 1) / d.u, Wb = (d.W - b + d.v - 1) / d.v;
+    long long total = (long long)d.N * Ha * Wb * d.C;
+    if (total <= 0) return GBCONV_OK;
+    unsigned g = grid_for(total, 256);
+    cudaError_t e;
+    if (d.out_dtype == GBCONV_F32)
+        e = launch_pdl(zero_phase<float>, dim3(g), dim3(256), 0, st, (float *)dx, d.N, d.H, d.W,
+                       d.C, d.u, d.v, a, b);
+    else
+        e = launch_pdl(zero_phase<__nv_bfloat16>, dim3(g), dim3(256), 0, st, (__nv_bfloat16 *)dx,
+                       d.N, d.H, d.W, d.C, d.u, d.v, a, b);
     return cuda_status(e);
 }
 

@@ -51,6 +51,10 @@ gbconv_status_t launch_reduce_slices(const float *ws, int slices, long long n, f
 gbconv_status_t launch_bias_grad(const Dims &d, const void *g, float *db, float *ws,
                                  int slices, cudaStream_t st);
 gbconv_status_t launch_rotate_filter(const Dims &d, const void *w, void *w_rot, cudaStream_t st);
+// w[k][r][s][c] -> wT[c][r][s][k] (BF16)
+gbconv_status_t launch_transpose_filter(const Dims &d, const void *w, void *wt, cudaStream_t st);
+// zeroes dx at rows u*h' + a, columns v*w' + b (NHWC, out_dtype of d)
+gbconv_status_t launch_zero_phase(const Dims &d, void *dx, int a, int b, cudaStream_t st);
 gbconv_status_t launch_quantize_e4m3(const void *in, int in_dtype, long long rows, long long len,
                                      uint8_t *out, float *scale, cudaStream_t st);
 
@@ -73,7 +77,12 @@ bool tc_fwd_shift_preferred(const Dims &d, int block_n);  // automatic choice
 gbconv_status_t launch_tc_fwd_shift(const Dims &d, const TcConfig &cfg, const void *x,
                                     const void *w, const float *bias, const float *x_scale,
                                     const float *w_scale, void *y, cudaStream_t st);
-// tc_fwd_t.cu: stride-1 band kernel with output channels on the MMA's M.
+// tc_fwd_t.cu: band kernel with output channels on the MMA's M (strides by
+// phase decomposition; 1x1 stride-1 layers as a flat GEMM), and the data
+// gradient of strided layers by sub-pixel phases on the same kernel.
+bool tc_dgrad_t_supported(const Dims &d);
+gbconv_status_t launch_tc_dgrad_t(const Dims &d, const void *dy, const void *wT, void *dx,
+                                  cudaStream_t st);
 int tc_fwd_t_tile(const Dims &d);  // output-channel tile (64 / 128), 0 if unsuitable
 gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, const float *bias,
                                 const float *x_scale, const float *w_scale, void *y,

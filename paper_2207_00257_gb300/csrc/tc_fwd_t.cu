@@ -84,6 +84,10 @@ struct TParams {
     int wx_log2, TR, n_pos;  // n_pos = TR * Wx positions per tile (MMA N)
     int flat;                // 1x1 stride-1 unpadded: x and y as [N*H*W] rows, tiles of n_pos rows
     int M;                   // flat: N*H*W
+    // output position (n, p, q) of the P x Q grid is y row
+    // (n*out_H + p*ou + oa)*out_W + q*ov + ob (forward: the grid is y itself;
+    // data gradient: one sub-pixel phase of dx)
+    int out_H, out_W, ou, ov, oa, ob;
     // phase f: band origin (column b - pw, row offset a - ph), taps [end[f-1], end[f])
     int n_phase;
     int ph_w0[MAX_PHASES], ph_h0[MAX_PHASES], ph_end[MAX_PHASES];
@@ -434,18 +438,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
             };
             // epilogue math and stores of chunk j from v
             auto process = [&](int j, const uint32_t (&v)[32]) {
-                size_t yrow;  // y row of the chunk's first position
-                int nvalid;   // positions of the chunk inside y
+                size_t yrow;    // y row of the chunk's first position
+                size_t ystep;   // y rows between consecutive positions
+                int nvalid;     // positions of the chunk inside y
                 if (prm.flat) {
                     const int m0 = p0 + 32 * j;
                     if (m0 >= prm.M) return;
                     yrow = (size_t)m0;
+                    ystep = 1;
                     nvalid = prm.M - m0;
                 } else {
                     const int p = p0 + ((32 * j) >> prm.wx_log2);
                     const int q0 = (32 * j) & wx_mask;
                     if (p >= prm.P || q0 >= prm.Q) return;
-                    yrow = ((size_t)n * prm.P + p) * prm.Q + q0;
+                    yrow = ((size_t)n * prm.out_H + (size_t)p * prm.ou + prm.oa) * prm.out_W + prm.ob +
+                           (size_t)q0 * prm.ov;
+                    ystep = (size_t)prm.ov;
                     nvalid = prm.Q - q0;
                 }
                 const int kw = kt * KT + chb0;                                // first channel of the warp
@@ -500,7 +508,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                         const int k = kw + 8 * c;
                         if (e < nvalid && k < prm.K)
                             *reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(prm.y) +
-                                                       (yrow + e) * prm.K + k) = val;
+                                                       (yrow + e * ystep) * prm.K + k) = val;
                     }
                 } else {
                     const int k = kt * KT + krow;
@@ -514,7 +522,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                             if (FP8) a = a * scl;
                             a = a + bia;
                             if (prm.relu) a = fmaxf(a, 0.f);
-                            if (e0 + i < nvalid) yf[(yrow + e0 + i) * prm.K + k] = a;
+                            if (e0 + i < nvalid) yf[(yrow + (e0 + i) * ystep) * prm.K + k] = a;
                         }
                     }
                 }
@@ -547,6 +555,8 @@ struct TPlan {
     int flat, n_pos, k_tiles;
     long long num_tiles;
 };
+
+bool plan_memory(int kt, long long w_tiles, TPlan *pl, TPlan &p);
 
 // A 1x1, stride-1, unpadded layer is a plain GEMM over the N*H*W positions.
 bool is_flat(const Dims &d) {
@@ -631,11 +641,18 @@ bool make_plan(const Dims &d, int kt, TPlan *pl) {
         p.num_tiles = (long long)d.N * ((d.P + p.TR - 1) / p.TR) * k_tiles;
         p.n_pos = p.TR << p.wx_log2;
     }
+    return plan_memory(kt, (long long)d.R * d.S * p.c_blocks, pl, p);
+}
+
+// Shared-memory split of a plan whose geometry (band size, channel blocks,
+// channel tiles) is set: the filter resident when there is one channel tile
+// and it fits beside two bands, else streamed through a ring of tiles.
+bool plan_memory(int kt, long long w_tiles, TPlan *pl, TPlan &p) {
     const int epi = kt == 128 ? epi_total<128>() : epi_total<64>();
     const int budget = SMEM_LIMIT - SMEM_ALIGN - BAR_BYTES - epi;
     const int wtile = kt * 128;
-    const long long w_total = (long long)d.R * d.S * p.c_blocks * wtile;
-    if (k_tiles == 1 && w_total + 2ll * p.band_stride <= budget) {
+    const long long w_total = w_tiles * wtile;
+    if (p.k_tiles == 1 && w_total + 2ll * p.band_stride <= budget) {
         p.w_resident = 1;
         p.stages_a = (int)std::min<long long>(MAX_SA, (budget - w_total) / p.band_stride);
         p.stages_b = 0;
@@ -738,6 +755,10 @@ gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, con
     prm.N = d.N;
     prm.P = d.P;
     prm.Q = d.Q;
+    prm.out_H = d.P;
+    prm.out_W = d.Q;
+    prm.ou = prm.ov = 1;
+    prm.oa = prm.ob = 0;
     prm.K = d.K;
     prm.u = d.u;
     prm.RS = d.R * d.S;
@@ -771,6 +792,188 @@ gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, con
     const int grid = std::min(prm.num_tiles, sm_count());
     if (kt == 64) return fp8 ? launch<64, true>(prm, smem, grid, st) : launch<64, false>(prm, smem, grid, st);
     return fp8 ? launch<128, true>(prm, smem, grid, st) : launch<128, false>(prm, smem, grid, st);
+}
+
+// ---------------------------------------------------------------------------
+// Data gradient of a strided layer by sub-pixel phases (the transposed
+// convolution of the backward pass, paper Sec. 5.B):
+//
+//   dx[n, u*h' + a, v*w' + b, c] = sum_{k, r in R_a, s in S_b}
+//       dy[n, h' + off_r, w' + off_s, k] * w[k, r, s, c]
+//
+// with R_a = {r : (a + ph - r*dh) divisible by u}, off_r = (a + ph - r*dh) / u
+// (S_b, off_s likewise). Each output phase (a, b) is a stride-1 correlation of
+// dy with the taps of R_a x S_b at offsets (off_r, off_s); it runs on the band
+// kernel with dy as input (K channels), the filter transposed to
+// wT[c][r*S + s][k], and the output positions scattered to dx rows
+// u*h' + a, columns v*w' + b. Phases without taps are zero.
+
+namespace {
+
+struct PhaseTaps {
+    int n;                      // taps
+    int off_min_r, off_max_r, off_min_s, off_max_s;
+    int t[MAX_TAPS], off_r[MAX_TAPS], off_s[MAX_TAPS];
+};
+
+void phase_taps(const Dims &d, int a, int b, PhaseTaps *pt) {
+    pt->n = 0;
+    pt->off_min_r = pt->off_min_s = 1 << 30;
+    pt->off_max_r = pt->off_max_s = -(1 << 30);
+    for (int r = 0; r < d.R; ++r) {
+        const int nr = a + d.ph - r * d.dh;
+        if (((nr % d.u) + d.u) % d.u) continue;
+        for (int s = 0; s < d.S; ++s) {
+            const int ns = b + d.pw - s * d.dw;
+            if (((ns % d.v) + d.v) % d.v) continue;
+            const int orr = nr / d.u, os = ns / d.v;  // exact (possibly negative) quotients
+            pt->t[pt->n] = r * d.S + s;
+            pt->off_r[pt->n] = orr;
+            pt->off_s[pt->n] = os;
+            pt->off_min_r = std::min(pt->off_min_r, orr);
+            pt->off_max_r = std::max(pt->off_max_r, orr);
+            pt->off_min_s = std::min(pt->off_min_s, os);
+            pt->off_max_s = std::max(pt->off_max_s, os);
+            ++pt->n;
+        }
+    }
+}
+
+// Geometry and memory plan of one phase; false if it does not fit the kernel.
+bool dgrad_phase_plan(const Dims &d, const PhaseTaps &pt, int Ha, int Wb, int kt, TPlan *pl) {
+    const int ke = 64;  // BF16
+    const int ispan = pt.off_max_r - pt.off_min_r, jspan = pt.off_max_s - pt.off_min_s;
+    int wx = 32;
+    while (wx < Wb + jspan) wx *= 2;
+    if (wx > NPOS) return false;
+    TPlan p{};
+    p.k_tiles = (d.C + kt - 1) / kt;
+    p.c_blocks = (d.K + ke - 1) / ke;
+    p.wx_log2 = ilog2(wx);
+    const int tr_max = NPOS / wx;
+    const int row_tiles = std::max(1, (Ha + tr_max - 1) / tr_max);
+    p.TR = std::max(1, (Ha + row_tiles - 1) / row_tiles);
+    p.nr = p.TR + ispan;
+    if (p.nr > 256) return false;
+    p.band_bytes = 128 * wx * p.nr;
+    p.band_stride = (p.band_bytes + jspan * 128 + 1023) / 1024 * 1024;
+    if (p.band_stride > 80 * 1024) return false;
+    p.n_phase = 1;
+    p.n_pos = p.TR << p.wx_log2;
+    p.num_tiles = (long long)d.N * ((Ha + p.TR - 1) / p.TR) * p.k_tiles;
+    return plan_memory(kt, (long long)pt.n * p.c_blocks, pl, p);
+}
+
+int dgrad_tile(const Dims &d) { return d.C <= 64 ? 64 : 128; }
+
+}  // namespace
+
+bool tc_dgrad_t_supported(const Dims &d) {
+    if (d.layout != GBCONV_NHWC || d.in_dtype != GBCONV_BF16) return false;
+    if (d.out_dtype != GBCONV_BF16 && d.out_dtype != GBCONV_F32) return false;
+    if (d.C % 8 || d.K % 8) return false;
+    if (d.M() >= (1ll << 31) || (long long)d.N * d.H * d.W >= (1ll << 31)) return false;
+    if (d.R * d.S > MAX_TAPS) return false;
+    const int kt = dgrad_tile(d);
+    for (int a = 0; a < std::min(d.u, d.H); ++a)
+        for (int b = 0; b < std::min(d.v, d.W); ++b) {
+            PhaseTaps pt;
+            phase_taps(d, a, b, &pt);
+            if (pt.n == 0) continue;
+            TPlan pl;
+            const int Ha = (d.H - a + d.u - 1) / d.u, Wb = (d.W - b + d.v - 1) / d.v;
+            if (!dgrad_phase_plan(d, pt, Ha, Wb, kt, &pl)) return false;
+            if (pl.num_tiles >= (1ll << 31)) return false;
+        }
+    return true;
+}
+
+gbconv_status_t launch_tc_dgrad_t(const Dims &d, const void *dy, const void *wT, void *dx,
+                                  cudaStream_t st) {
+    if (!tc_dgrad_t_supported(d)) return GBCONV_ERR_UNSUPPORTED;
+    if ((long long)d.N * d.H * d.W == 0) return GBCONV_OK;
+    if (reinterpret_cast<uintptr_t>(dx) % 16) return GBCONV_ERR_ALIGNMENT;
+    const int kt = dgrad_tile(d);
+    const int ke = 64, eb = 2;
+    const bool of32 = d.out_dtype == GBCONV_F32;
+    for (int a = 0; a < std::min(d.u, d.H); ++a)
+        for (int b = 0; b < std::min(d.v, d.W); ++b) {
+            const int Ha = (d.H - a + d.u - 1) / d.u, Wb = (d.W - b + d.v - 1) / d.v;
+            PhaseTaps pt;
+            phase_taps(d, a, b, &pt);
+            gbconv_status_t s;
+            if (pt.n == 0) {  // no tap reaches these positions
+                s = launch_zero_phase(d, dx, a, b, st);
+                if (s != GBCONV_OK) return s;
+                continue;
+            }
+            TPlan pl;
+            if (!dgrad_phase_plan(d, pt, Ha, Wb, kt, &pl)) return GBCONV_ERR_UNSUPPORTED;
+            TParams prm;
+            memset(&prm, 0, sizeof(prm));
+            // dy [N][P][Q][K]: bands of nr rows x Wx columns, stride 1
+            uint64_t xd[4] = {(uint64_t)d.K, (uint64_t)d.Q, (uint64_t)d.P, (uint64_t)d.N};
+            uint64_t xs[3] = {(uint64_t)d.K * eb, (uint64_t)d.Q * d.K * eb,
+                              (uint64_t)d.P * d.Q * d.K * eb};
+            uint32_t xb[4] = {(uint32_t)ke, (uint32_t)(1 << pl.wx_log2), (uint32_t)pl.nr, 1};
+            s = encode_tiled(&prm.tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, dy, xd, xs, xb,
+                             CU_TENSOR_MAP_SWIZZLE_128B);
+            if (s != GBCONV_OK) return s;
+            // wT [C][R*S][K]
+            uint64_t wd[3] = {(uint64_t)d.K, (uint64_t)d.R * d.S, (uint64_t)d.C};
+            uint64_t wstr[2] = {(uint64_t)d.K * eb, (uint64_t)d.R * d.S * d.K * eb};
+            uint32_t wbx[3] = {(uint32_t)ke, 1, (uint32_t)kt};
+            s = encode_tiled(&prm.tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, wT, wd, wstr, wbx,
+                             CU_TENSOR_MAP_SWIZZLE_128B);
+            if (s != GBCONV_OK) return s;
+            prm.y = dx;
+            prm.N = d.N;
+            prm.P = Ha;
+            prm.Q = Wb;
+            prm.K = d.C;
+            prm.out_H = d.H;
+            prm.out_W = d.W;
+            prm.ou = d.u;
+            prm.ov = d.v;
+            prm.oa = a;
+            prm.ob = b;
+            prm.u = 1;
+            prm.RS = pt.n;
+            prm.wx_log2 = pl.wx_log2;
+            prm.n_phase = 1;
+            prm.ph_w0[0] = pt.off_min_s;
+            prm.ph_h0[0] = pt.off_min_r;
+            prm.ph_end[0] = pt.n;
+            for (int i = 0; i < pt.n; ++i) {
+                prm.tap_t[i] = (uint16_t)pt.t[i];
+                prm.tap_shift[i] = (uint16_t)(((pt.off_r[i] - pt.off_min_r) << pl.wx_log2) +
+                                              (pt.off_s[i] - pt.off_min_s));
+            }
+            prm.TR = pl.TR;
+            prm.n_pos = pl.n_pos;
+            prm.flat = 0;
+            prm.c_blocks = pl.c_blocks;
+            prm.k_tiles = pl.k_tiles;
+            prm.p_tiles = (Ha + pl.TR - 1) / pl.TR;
+            prm.num_tiles = (int)pl.num_tiles;
+            prm.band_bytes = pl.band_bytes;
+            prm.band_stride = pl.band_stride;
+            prm.w_resident = pl.w_resident;
+            prm.stages_a = pl.stages_a;
+            prm.stages_b = pl.stages_b;
+            prm.relu = 0;
+            prm.out_f32 = of32;
+            prm.guard = make_guard();
+            if (!prm.guard.err) return GBCONV_ERR_CUDA;
+            const int w_slots = pl.w_resident ? pt.n * pl.c_blocks : pl.stages_b;
+            const size_t smem = (size_t)SMEM_ALIGN + (size_t)pl.stages_a * pl.band_stride +
+                                (size_t)w_slots * kt * 128 +
+                                (kt == 128 ? epi_total<128>() : epi_total<64>()) + BAR_BYTES;
+            const int grid = std::min(prm.num_tiles, sm_count());
+            s = kt == 64 ? launch<64, false>(prm, smem, grid, st) : launch<128, false>(prm, smem, grid, st);
+            if (s != GBCONV_OK) return s;
+        }
+    return GBCONV_OK;
 }
 
 }  // namespace gbc

@@ -130,9 +130,12 @@ def test_workspace_sizes():
     assert B.gbconv_workspace_size(B.GBCONV_OP_FWD, p) == (B.GBCONV_OK, 0)
     s, n = B.gbconv_workspace_size(B.GBCONV_OP_DGRAD, p)
     assert s == B.GBCONV_OK and n == (128 * 9 * 128 * 2 + 255) // 256 * 256
-    # stride 2 data gradient runs on the CUDA-core kernel: no workspace
+    # stride 2 (BF16 NHWC): sub-pixel phases hold the transposed filter
     p2 = B.problem(32, 128, 56, 56, 128, 3, 3, 2, 1, 1)
-    assert B.gbconv_workspace_size(B.GBCONV_OP_DGRAD, p2) == (B.GBCONV_OK, 0)
+    assert B.gbconv_workspace_size(B.GBCONV_OP_DGRAD, p2) == (B.GBCONV_OK, n)
+    # FP32 NCHW runs on the CUDA-core kernel: no workspace
+    p3 = B.problem(2, 8, 16, 16, 8, 3, 3, 2, 1, 1, B.GBCONV_F32, B.GBCONV_F32, B.GBCONV_NCHW)
+    assert B.gbconv_workspace_size(B.GBCONV_OP_DGRAD, p3) == (B.GBCONV_OK, 0)
     s, n = B.gbconv_workspace_size(B.GBCONV_OP_WGRAD, p)
     s2, cfg = B.gbconv_get_config(B.GBCONV_OP_WGRAD, p)
     assert s == s2 == B.GBCONV_OK and cfg.split_k >= 1

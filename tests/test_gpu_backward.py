@@ -55,7 +55,7 @@ BWD_SHAPES = [
     ConvShape(2, 32, 8, 8, 48, 1, 1, 1, 0, 1),
     ConvShape(1, 16, 12, 12, 24, 3, 3, 1, 2, 2),         # dilation 2, pad' = 2
     ConvShape(2, 24, 10, 10, 16, 5, 5, 1, 1, 1),         # pad < d(R-1): asymmetric rotation pad
-    ConvShape(2, 32, 11, 11, 32, 3, 3, 2, 1, 1),         # stride 2: CUDA-core dgrad
+    ConvShape(2, 32, 11, 11, 32, 3, 3, 2, 1, 1),         # stride 2: sub-pixel phase dgrad
     ConvShape(2, 8, 9, 7, 16, 3, 2, (2, 1), (1, 0), (1, 2)),
 ]
 
@@ -70,6 +70,50 @@ def test_bf16_backward_small(sh):
 def test_bf16_dgrad_bf16_out(sh):
     e = _grads(sh, torch.bfloat16, seed=31, out_dtype=torch.bfloat16)
     assert e["dx"] <= TOL_BF16_OUT, e
+
+
+# Data gradient of strided (or over-padded) BF16 NHWC layers: one stride-1
+# band-kernel launch per sub-pixel phase of dx, zero fill for phases no tap reaches.
+PHASE_DGRAD_SHAPES = [
+    ConvShape(2, 128, 17, 15, 128, 3, 3, 2, 1, 1),    # ragged, 4 phases with 1-4 taps
+    ConvShape(2, 64, 14, 13, 96, 1, 1, 2, 0, 1),      # 1x1 stride 2: 3 of 4 phases zero
+    ConvShape(1, 64, 23, 19, 64, 5, 5, 2, 2, 1),      # offsets -1..1 in each phase
+    ConvShape(1, 48, 21, 21, 64, 3, 3, 2, 2, 2),      # stride 2, dilation 2: odd phases zero
+    ConvShape(1, 64, 25, 25, 32, 3, 3, 3, 1, 1),      # stride 3: 9 phases of one tap
+    ConvShape(1, 32, 12, 12, 200, 3, 3, 2, 1, 1),     # 32 output channels, 200 reduction channels
+    ConvShape(1, 192, 10, 10, 64, 3, 3, 2, 1, 1),     # 192 output channels: two channel tiles
+    ConvShape(1, 32, 9, 9, 32, 3, 3, 1, 3, 1),        # stride 1, pad > d(R-1)
+    ConvShape(2, 32, 9, 16, 48, 3, 3, (2, 1), 1, 1),  # row stride only
+]
+
+
+@pytest.mark.parametrize("sh", PHASE_DGRAD_SHAPES, ids=_id)
+@pytest.mark.parametrize("out", ["f32", "bf16"])
+def test_bf16_dgrad_subpixel_phases(sh, out):
+    x, w, _, g = make_inputs(sh, 33, grad=True)
+    od = torch.float32 if out == "f32" else torch.bfloat16
+    wg, gg = w.bfloat16(), g.bfloat16()
+    dx = F.conv2d_dgrad(gg.cuda(), wg.cuda(), tuple(x.shape), sh.stride, sh.pad, sh.dil, "NHWC",
+                        out_dtype=od)
+    F.device_error()
+    ref, bound = oracle.conv2d_dgrad(oconv(sh), f64(gg), f64(wg), with_bound=True)
+    err = oracle.max_normalised_error(f64(dx).reshape(-1), ref.reshape(-1), bound.reshape(-1))
+    assert err <= (TOL_ACC32 if out == "f32" else TOL_BF16_OUT), err
+
+
+def test_dgrad_subpixel_integer_exact():
+    """Integer operands: every partial sum is exact in FP32, so the phase
+    kernel must reproduce the oracle bit for bit (stride 2, 3x3, FP32 out)."""
+    sh = ConvShape(2, 64, 15, 13, 64, 3, 3, 2, 1, 1)
+    gen = torch.Generator().manual_seed(34)
+    P, Q = sh.P, sh.Q
+    g = torch.randint(-4, 5, (sh.N, P, Q, sh.K), generator=gen).float()
+    w = torch.randint(-4, 5, (sh.K, sh.R, sh.S, sh.C), generator=gen).float()
+    dx = F.conv2d_dgrad(g.bfloat16().cuda(), w.bfloat16().cuda(), (sh.N, sh.H, sh.W, sh.C),
+                        sh.stride, sh.pad, sh.dil, "NHWC", out_dtype=torch.float32)
+    F.device_error()
+    ref = oracle.conv2d_dgrad(oconv(sh), f64(g), f64(w))
+    assert np.array_equal(f64(dx).reshape(-1), np.asarray(ref).reshape(-1))
 
 
 @pytest.mark.parametrize("sh", [ConvShape(2, 5, 9, 8, 7, 3, 3, 1, 1, 1, "NCHW"),
