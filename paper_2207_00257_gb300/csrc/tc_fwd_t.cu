@@ -88,6 +88,13 @@ struct TParams {
     // (n*out_H + p*ou + oa)*out_W + q*ov + ob (forward: the grid is y itself;
     // data gradient: one sub-pixel phase of dx)
     int out_H, out_W, ou, ov, oa, ob;
+    // data gradient: n_ophase > 0 output phases in one launch; phase op owns
+    // tiles [op_tile0[op], op_tile0[op+1]), its band origin and taps are phase
+    // op of ph_* / tap_*, its grid is op_P x op_Q at offsets (op_oa, op_ob)
+    int n_ophase;
+    int op_tile0[MAX_PHASES + 1];
+    int op_P[MAX_PHASES], op_Q[MAX_PHASES], op_oa[MAX_PHASES], op_ob[MAX_PHASES];
+    int op_ptiles[MAX_PHASES];
     // phase f: band origin (column b - pw, row offset a - ph), taps [end[f-1], end[f])
     int n_phase;
     int ph_w0[MAX_PHASES], ph_h0[MAX_PHASES], ph_end[MAX_PHASES];
@@ -103,18 +110,44 @@ struct TParams {
 
 static_assert(sizeof(TParams) <= 4096, "transposed kernel parameters too large");
 
-// Tile -> (image n, first output row p0, output-channel tile kt); flat
-// layers: n = 0 and p0 = first position row of the tile.
-__device__ __forceinline__ void tdecode(const TParams &p, int tile, int &n, int &p0, int &kt) {
-    kt = tile % p.k_tiles;
-    const int mt = tile / p.k_tiles;
-    if (p.flat) {
-        n = 0;
-        p0 = mt * p.n_pos;
-        return;
+// One tile: image n, first output row p0 (flat layers: n = 0, p0 = first
+// position row), output-channel tile kt, the phases [f0, f1) its bands come
+// from, and the P x Q grid and offsets its outputs go to.
+struct Tile {
+    int n, p0, kt, f0, f1, P, Q, oa, ob;
+};
+
+__device__ __forceinline__ Tile tdecode(const TParams &p, int tile) {
+    Tile t;
+    int lt = tile, ptiles = p.p_tiles;
+    t.f0 = 0;
+    t.f1 = p.n_phase;
+    t.P = p.P;
+    t.Q = p.Q;
+    t.oa = p.oa;
+    t.ob = p.ob;
+    if (p.n_ophase) {
+        int op = 0;
+        while (op + 1 < p.n_ophase && tile >= p.op_tile0[op + 1]) ++op;
+        lt = tile - p.op_tile0[op];
+        ptiles = p.op_ptiles[op];
+        t.f0 = op;
+        t.f1 = op + 1;
+        t.P = p.op_P[op];
+        t.Q = p.op_Q[op];
+        t.oa = p.op_oa[op];
+        t.ob = p.op_ob[op];
     }
-    n = mt / p.p_tiles;
-    p0 = (mt - n * p.p_tiles) * p.TR;
+    t.kt = lt % p.k_tiles;
+    const int mt = lt / p.k_tiles;
+    if (p.flat) {
+        t.n = 0;
+        t.p0 = mt * p.n_pos;
+        return t;
+    }
+    t.n = mt / ptiles;
+    t.p0 = (mt - t.n * ptiles) * p.TR;
+    return t;
 }
 
 template <int KT, bool FP8>
@@ -207,11 +240,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
             int sa = 0, sb = 0;
             uint32_t pa = 0, pb = 0;
             int issued_a = 0, issued_b = 0;
+            if (prm.w_resident && !skip && prm.n_ophase) {
+                // data gradient: the first tile uses one phase's taps only, so
+                // the whole resident filter is issued up front
+                for (int seq = 0; seq < w_tiles; ++seq) {
+                    const int b = seq / wper, cb = seq / prm.RS, ti = seq - cb * prm.RS;
+                    if (seq % wper == 0)
+                        ptx::mbar_arrive_expect_tx(
+                            &wres[b], (uint32_t)(min(wper, w_tiles - b * wper) * W_TILE));
+                    ptx::tma_load_3d(sW + seq * W_TILE, &prm.tmW, &wres[b], cb * KE, prm.tap_t[ti], 0);
+                }
+                issued_w = w_tiles;
+            }
             for (int tile = blockIdx.x; ok && tile < prm.num_tiles; tile += gridDim.x) {
-                int n, p0, kt;
-                tdecode(prm, tile, n, p0, kt);
+                const Tile T = tdecode(prm, tile);
+                const int n = T.n, p0 = T.p0, kt = T.kt;
                 for (int cb = 0; ok && cb < prm.c_blocks; ++cb) {
-                    for (int f = 0; ok && f < prm.n_phase; ++f) {
+                    for (int f = T.f0; ok && f < T.f1; ++f) {
                         if (!ptx::mbar_wait(&emptyA[sa], pa ^ 1, lim, abort_flag)) {
                             fail();
                             ok = false;
@@ -311,10 +356,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                     break;
                 }
                 ptx::tc_fence_after();
+                const Tile T = tdecode(prm, tile);
                 const uint32_t d = tmem_base + (uint32_t)(acc * NPOS);
                 uint32_t accum = 0;
                 for (int cb = 0; ok && cb < prm.c_blocks; ++cb) {
-                    for (int f = 0; f < prm.n_phase; ++f) {
+                    for (int f = T.f0; f < T.f1; ++f) {
                         if (!ptx::mbar_wait(&fullA[sa], pa, lim, abort_flag)) {
                             fail();
                             ok = false;
@@ -326,7 +372,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                             uint32_t w_addr;
                             if (prm.w_resident) {
                                 const int seq = cb * prm.RS + ti;
-                                if (local == 0) {  // first tile: wait for this tile's group
+                                {  // this tile's group loaded (at once true after its first use)
                                     if (!ptx::mbar_wait(&wres[seq / wper], 0, lim, abort_flag)) {
                                         fail();
                                         ok = false;
@@ -393,8 +439,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
         const int nchunks = prm.n_pos >> 5;
         int local = 0;
         for (int tile = blockIdx.x; tile < prm.num_tiles; tile += gridDim.x, ++local) {
-            int n, p0, kt;
-            tdecode(prm, tile, n, p0, kt);
+            const Tile T = tdecode(prm, tile);
+            const int n = T.n, p0 = T.p0, kt = T.kt;
             const int acc = local & 1;
             const uint32_t aph = (local >> 1) & 1;
             // per-channel constants, fetched before the accumulator is ready
@@ -450,11 +496,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                 } else {
                     const int p = p0 + ((32 * j) >> prm.wx_log2);
                     const int q0 = (32 * j) & wx_mask;
-                    if (p >= prm.P || q0 >= prm.Q) return;
-                    yrow = ((size_t)n * prm.out_H + (size_t)p * prm.ou + prm.oa) * prm.out_W + prm.ob +
+                    if (p >= T.P || q0 >= T.Q) return;
+                    yrow = ((size_t)n * prm.out_H + (size_t)p * prm.ou + T.oa) * prm.out_W + T.ob +
                            (size_t)q0 * prm.ov;
                     ystep = (size_t)prm.ov;
-                    nvalid = prm.Q - q0;
+                    nvalid = T.Q - q0;
                 }
                 const int kw = kt * KT + chb0;                                // first channel of the warp
                 if (!prm.out_f32) {
@@ -839,32 +885,87 @@ void phase_taps(const Dims &d, int a, int b, PhaseTaps *pt) {
     }
 }
 
-// Geometry and memory plan of one phase; false if it does not fit the kernel.
-bool dgrad_phase_plan(const Dims &d, const PhaseTaps &pt, int Ha, int Wb, int kt, TPlan *pl) {
-    const int ke = 64;  // BF16
-    const int ispan = pt.off_max_r - pt.off_min_r, jspan = pt.off_max_s - pt.off_min_s;
+// All output phases of one data gradient, in one launch: common band shape
+// (Wx, TR, nr over the widest phase), phases with more taps first so their
+// longer tiles start early.
+struct DgradPlan {
+    TPlan pl;
+    int n_op;                          // phases with taps
+    int a[MAX_PHASES], b[MAX_PHASES];  // their offsets, in launch order
+    int Ha[MAX_PHASES], Wb[MAX_PHASES];
+    PhaseTaps taps[MAX_PHASES];
+    int n_zero;                        // phases no tap reaches
+    int za[MAX_PHASES], zb[MAX_PHASES];
+};
+
+int dgrad_tile(const Dims &d) { return d.C <= 64 ? 64 : 128; }
+
+bool dgrad_plan(const Dims &d, DgradPlan *dp) {
+    if (d.u > MAX_STRIDE || d.v > MAX_STRIDE || d.R * d.S > MAX_TAPS) return false;
+    const int kt = dgrad_tile(d), ke = 64;  // BF16
+    dp->n_op = dp->n_zero = 0;
+    int ispan = 0, jspan = 0, wneed = 0, hmax = 0;
+    for (int a = 0; a < std::min(d.u, d.H); ++a)
+        for (int b = 0; b < std::min(d.v, d.W); ++b) {
+            PhaseTaps &pt = dp->taps[dp->n_op];
+            phase_taps(d, a, b, &pt);
+            if (pt.n == 0) {
+                dp->za[dp->n_zero] = a;
+                dp->zb[dp->n_zero] = b;
+                ++dp->n_zero;
+                continue;
+            }
+            const int Ha = (d.H - a + d.u - 1) / d.u, Wb = (d.W - b + d.v - 1) / d.v;
+            dp->a[dp->n_op] = a;
+            dp->b[dp->n_op] = b;
+            dp->Ha[dp->n_op] = Ha;
+            dp->Wb[dp->n_op] = Wb;
+            ispan = std::max(ispan, pt.off_max_r - pt.off_min_r);
+            jspan = std::max(jspan, pt.off_max_s - pt.off_min_s);
+            wneed = std::max(wneed, Wb + pt.off_max_s - pt.off_min_s);
+            hmax = std::max(hmax, Ha);
+            ++dp->n_op;
+        }
+    // longest phases (most taps) first: a stable insertion sort of the phases
+    for (int i = 1; i < dp->n_op; ++i)
+        for (int j = i; j > 0 && dp->taps[j].n > dp->taps[j - 1].n; --j) {
+            std::swap(dp->taps[j], dp->taps[j - 1]);
+            std::swap(dp->a[j], dp->a[j - 1]);
+            std::swap(dp->b[j], dp->b[j - 1]);
+            std::swap(dp->Ha[j], dp->Ha[j - 1]);
+            std::swap(dp->Wb[j], dp->Wb[j - 1]);
+        }
+    if (dp->n_op == 0) return true;
     int wx = 32;
-    while (wx < Wb + jspan) wx *= 2;
+    while (wx < wneed) wx *= 2;
     if (wx > NPOS) return false;
-    TPlan p{};
+    TPlan &p = dp->pl;
+    p = TPlan{};
     p.k_tiles = (d.C + kt - 1) / kt;
     p.c_blocks = (d.K + ke - 1) / ke;
     p.wx_log2 = ilog2(wx);
     const int tr_max = NPOS / wx;
-    const int row_tiles = std::max(1, (Ha + tr_max - 1) / tr_max);
-    p.TR = std::max(1, (Ha + row_tiles - 1) / row_tiles);
+    const int row_tiles = std::max(1, (hmax + tr_max - 1) / tr_max);
+    p.TR = std::max(1, (hmax + row_tiles - 1) / row_tiles);
     p.nr = p.TR + ispan;
     if (p.nr > 256) return false;
     p.band_bytes = 128 * wx * p.nr;
     p.band_stride = (p.band_bytes + jspan * 128 + 1023) / 1024 * 1024;
     if (p.band_stride > 80 * 1024) return false;
-    p.n_phase = 1;
+    p.n_phase = dp->n_op;
     p.n_pos = p.TR << p.wx_log2;
-    p.num_tiles = (long long)d.N * ((Ha + p.TR - 1) / p.TR) * p.k_tiles;
-    return plan_memory(kt, (long long)pt.n * p.c_blocks, pl, p);
+    long long tiles = 0, taps = 0;
+    for (int i = 0; i < dp->n_op; ++i) {
+        tiles += (long long)d.N * ((dp->Ha[i] + p.TR - 1) / p.TR) * p.k_tiles;
+        taps += dp->taps[i].n;
+    }
+    if (taps > MAX_TAPS || tiles >= (1ll << 31)) return false;
+    p.num_tiles = tiles;
+    TPlan out;
+    if (!plan_memory(kt, taps * p.c_blocks, &out, p)) return false;
+    p = out;
+    return true;
 }
-
-int dgrad_tile(const Dims &d) { return d.C <= 64 ? 64 : 128; }
 
 }  // namespace
 
@@ -873,19 +974,8 @@ bool tc_dgrad_t_supported(const Dims &d) {
     if (d.out_dtype != GBCONV_BF16 && d.out_dtype != GBCONV_F32) return false;
     if (d.C % 8 || d.K % 8) return false;
     if (d.M() >= (1ll << 31) || (long long)d.N * d.H * d.W >= (1ll << 31)) return false;
-    if (d.R * d.S > MAX_TAPS) return false;
-    const int kt = dgrad_tile(d);
-    for (int a = 0; a < std::min(d.u, d.H); ++a)
-        for (int b = 0; b < std::min(d.v, d.W); ++b) {
-            PhaseTaps pt;
-            phase_taps(d, a, b, &pt);
-            if (pt.n == 0) continue;
-            TPlan pl;
-            const int Ha = (d.H - a + d.u - 1) / d.u, Wb = (d.W - b + d.v - 1) / d.v;
-            if (!dgrad_phase_plan(d, pt, Ha, Wb, kt, &pl)) return false;
-            if (pl.num_tiles >= (1ll << 31)) return false;
-        }
-    return true;
+    DgradPlan dp;
+    return dgrad_plan(d, &dp);
 }
 
 gbconv_status_t launch_tc_dgrad_t(const Dims &d, const void *dy, const void *wT, void *dx,
@@ -893,87 +983,83 @@ gbconv_status_t launch_tc_dgrad_t(const Dims &d, const void *dy, const void *wT,
     if (!tc_dgrad_t_supported(d)) return GBCONV_ERR_UNSUPPORTED;
     if ((long long)d.N * d.H * d.W == 0) return GBCONV_OK;
     if (reinterpret_cast<uintptr_t>(dx) % 16) return GBCONV_ERR_ALIGNMENT;
+    DgradPlan dp;
+    dgrad_plan(d, &dp);
+    for (int i = 0; i < dp.n_zero; ++i) {  // positions no tap reaches
+        gbconv_status_t s = launch_zero_phase(d, dx, dp.za[i], dp.zb[i], st);
+        if (s != GBCONV_OK) return s;
+    }
+    if (dp.n_op == 0) return GBCONV_OK;
+    const TPlan &pl = dp.pl;
     const int kt = dgrad_tile(d);
     const int ke = 64, eb = 2;
-    const bool of32 = d.out_dtype == GBCONV_F32;
-    for (int a = 0; a < std::min(d.u, d.H); ++a)
-        for (int b = 0; b < std::min(d.v, d.W); ++b) {
-            const int Ha = (d.H - a + d.u - 1) / d.u, Wb = (d.W - b + d.v - 1) / d.v;
-            PhaseTaps pt;
-            phase_taps(d, a, b, &pt);
-            gbconv_status_t s;
-            if (pt.n == 0) {  // no tap reaches these positions
-                s = launch_zero_phase(d, dx, a, b, st);
-                if (s != GBCONV_OK) return s;
-                continue;
-            }
-            TPlan pl;
-            if (!dgrad_phase_plan(d, pt, Ha, Wb, kt, &pl)) return GBCONV_ERR_UNSUPPORTED;
-            TParams prm;
-            memset(&prm, 0, sizeof(prm));
-            // dy [N][P][Q][K]: bands of nr rows x Wx columns, stride 1
-            uint64_t xd[4] = {(uint64_t)d.K, (uint64_t)d.Q, (uint64_t)d.P, (uint64_t)d.N};
-            uint64_t xs[3] = {(uint64_t)d.K * eb, (uint64_t)d.Q * d.K * eb,
-                              (uint64_t)d.P * d.Q * d.K * eb};
-            uint32_t xb[4] = {(uint32_t)ke, (uint32_t)(1 << pl.wx_log2), (uint32_t)pl.nr, 1};
-            s = encode_tiled(&prm.tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, dy, xd, xs, xb,
-                             CU_TENSOR_MAP_SWIZZLE_128B);
-            if (s != GBCONV_OK) return s;
-            // wT [C][R*S][K]
-            uint64_t wd[3] = {(uint64_t)d.K, (uint64_t)d.R * d.S, (uint64_t)d.C};
-            uint64_t wstr[2] = {(uint64_t)d.K * eb, (uint64_t)d.R * d.S * d.K * eb};
-            uint32_t wbx[3] = {(uint32_t)ke, 1, (uint32_t)kt};
-            s = encode_tiled(&prm.tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, wT, wd, wstr, wbx,
-                             CU_TENSOR_MAP_SWIZZLE_128B);
-            if (s != GBCONV_OK) return s;
-            prm.y = dx;
-            prm.N = d.N;
-            prm.P = Ha;
-            prm.Q = Wb;
-            prm.K = d.C;
-            prm.out_H = d.H;
-            prm.out_W = d.W;
-            prm.ou = d.u;
-            prm.ov = d.v;
-            prm.oa = a;
-            prm.ob = b;
-            prm.u = 1;
-            prm.RS = pt.n;
-            prm.wx_log2 = pl.wx_log2;
-            prm.n_phase = 1;
-            prm.ph_w0[0] = pt.off_min_s;
-            prm.ph_h0[0] = pt.off_min_r;
-            prm.ph_end[0] = pt.n;
-            for (int i = 0; i < pt.n; ++i) {
-                prm.tap_t[i] = (uint16_t)pt.t[i];
-                prm.tap_shift[i] = (uint16_t)(((pt.off_r[i] - pt.off_min_r) << pl.wx_log2) +
-                                              (pt.off_s[i] - pt.off_min_s));
-            }
-            prm.TR = pl.TR;
-            prm.n_pos = pl.n_pos;
-            prm.flat = 0;
-            prm.c_blocks = pl.c_blocks;
-            prm.k_tiles = pl.k_tiles;
-            prm.p_tiles = (Ha + pl.TR - 1) / pl.TR;
-            prm.num_tiles = (int)pl.num_tiles;
-            prm.band_bytes = pl.band_bytes;
-            prm.band_stride = pl.band_stride;
-            prm.w_resident = pl.w_resident;
-            prm.stages_a = pl.stages_a;
-            prm.stages_b = pl.stages_b;
-            prm.relu = 0;
-            prm.out_f32 = of32;
-            prm.guard = make_guard();
-            if (!prm.guard.err) return GBCONV_ERR_CUDA;
-            const int w_slots = pl.w_resident ? pt.n * pl.c_blocks : pl.stages_b;
-            const size_t smem = (size_t)SMEM_ALIGN + (size_t)pl.stages_a * pl.band_stride +
-                                (size_t)w_slots * kt * 128 +
-                                (kt == 128 ? epi_total<128>() : epi_total<64>()) + BAR_BYTES;
-            const int grid = std::min(prm.num_tiles, sm_count());
-            s = kt == 64 ? launch<64, false>(prm, smem, grid, st) : launch<128, false>(prm, smem, grid, st);
-            if (s != GBCONV_OK) return s;
+    TParams prm;
+    memset(&prm, 0, sizeof(prm));
+    // dy [N][P][Q][K]: bands of nr rows x Wx columns, stride 1
+    uint64_t xd[4] = {(uint64_t)d.K, (uint64_t)d.Q, (uint64_t)d.P, (uint64_t)d.N};
+    uint64_t xs[3] = {(uint64_t)d.K * eb, (uint64_t)d.Q * d.K * eb, (uint64_t)d.P * d.Q * d.K * eb};
+    uint32_t xb[4] = {(uint32_t)ke, (uint32_t)(1 << pl.wx_log2), (uint32_t)pl.nr, 1};
+    gbconv_status_t s = encode_tiled(&prm.tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, dy, xd, xs, xb,
+                                     CU_TENSOR_MAP_SWIZZLE_128B);
+    if (s != GBCONV_OK) return s;
+    // wT [C][R*S][K]
+    uint64_t wd[3] = {(uint64_t)d.K, (uint64_t)d.R * d.S, (uint64_t)d.C};
+    uint64_t wstr[2] = {(uint64_t)d.K * eb, (uint64_t)d.R * d.S * d.K * eb};
+    uint32_t wbx[3] = {(uint32_t)ke, 1, (uint32_t)kt};
+    s = encode_tiled(&prm.tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, wT, wd, wstr, wbx,
+                     CU_TENSOR_MAP_SWIZZLE_128B);
+    if (s != GBCONV_OK) return s;
+    prm.y = dx;
+    prm.N = d.N;
+    prm.K = d.C;
+    prm.out_H = d.H;
+    prm.out_W = d.W;
+    prm.ou = d.u;
+    prm.ov = d.v;
+    prm.u = 1;
+    prm.wx_log2 = pl.wx_log2;
+    prm.n_phase = dp.n_op;
+    prm.n_ophase = dp.n_op;
+    int nt = 0, tile0 = 0;
+    for (int op = 0; op < dp.n_op; ++op) {
+        const PhaseTaps &pt = dp.taps[op];
+        prm.ph_w0[op] = pt.off_min_s;
+        prm.ph_h0[op] = pt.off_min_r;
+        for (int i = 0; i < pt.n; ++i, ++nt) {
+            prm.tap_t[nt] = (uint16_t)pt.t[i];
+            prm.tap_shift[nt] = (uint16_t)(((pt.off_r[i] - pt.off_min_r) << pl.wx_log2) +
+                                           (pt.off_s[i] - pt.off_min_s));
         }
-    return GBCONV_OK;
+        prm.ph_end[op] = nt;
+        prm.op_P[op] = dp.Ha[op];
+        prm.op_Q[op] = dp.Wb[op];
+        prm.op_oa[op] = dp.a[op];
+        prm.op_ob[op] = dp.b[op];
+        prm.op_ptiles[op] = (dp.Ha[op] + pl.TR - 1) / pl.TR;
+        prm.op_tile0[op] = tile0;
+        tile0 += d.N * prm.op_ptiles[op] * pl.k_tiles;
+    }
+    prm.op_tile0[dp.n_op] = tile0;
+    prm.RS = nt;
+    prm.TR = pl.TR;
+    prm.n_pos = pl.n_pos;
+    prm.c_blocks = pl.c_blocks;
+    prm.k_tiles = pl.k_tiles;
+    prm.num_tiles = (int)pl.num_tiles;
+    prm.band_bytes = pl.band_bytes;
+    prm.band_stride = pl.band_stride;
+    prm.w_resident = pl.w_resident;
+    prm.stages_a = pl.stages_a;
+    prm.stages_b = pl.stages_b;
+    prm.out_f32 = d.out_dtype == GBCONV_F32;
+    prm.guard = make_guard();
+    if (!prm.guard.err) return GBCONV_ERR_CUDA;
+    const int w_slots = pl.w_resident ? nt * pl.c_blocks : pl.stages_b;
+    const size_t smem = (size_t)SMEM_ALIGN + (size_t)pl.stages_a * pl.band_stride +
+                        (size_t)w_slots * kt * 128 +
+                        (kt == 128 ? epi_total<128>() : epi_total<64>()) + BAR_BYTES;
+    const int grid = std::min(prm.num_tiles, sm_count());
+    return kt == 64 ? launch<64, false>(prm, smem, grid, st) : launch<128, false>(prm, smem, grid, st);
 }
 
 }  // namespace gbc
