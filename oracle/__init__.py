@@ -61,6 +61,12 @@ def _load():
             lib.oracle_conv2d_wgrad.argtypes = [_i64p, _f64p, _f64p, _i64p, ctypes.c_int64,
                                                 _f64p, _f64p, ctypes.c_int]
             lib.oracle_conv2d_bgrad.argtypes = [_i64p, _f64p, _f64p, _f64p]
+            lib.oracle_conv2d_fwd_fused.argtypes = [_i64p, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                                    ctypes.c_int, _i64p, ctypes.c_int64, _f64p,
+                                                    _f64p, ctypes.c_int]
+            lib.oracle_bn_fold.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p,
+                                           ctypes.c_double, _f64p, _f64p, _f64p]
+            lib.oracle_bn_fold.restype = None
             lib.oracle_round_bf16.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
             lib.oracle_bf16_to_f64.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
             lib.oracle_quant_e4m3.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
@@ -69,7 +75,7 @@ def _load():
                                                     ctypes.c_int64, ctypes.c_void_p,
                                                     ctypes.c_void_p]
             for f in ("oracle_output_dims", "oracle_conv2d_fwd", "oracle_conv2d_dgrad",
-                      "oracle_conv2d_wgrad", "oracle_conv2d_bgrad"):
+                      "oracle_conv2d_wgrad", "oracle_conv2d_bgrad", "oracle_conv2d_fwd_fused"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -147,6 +153,47 @@ def conv2d_fwd(p: Conv, x, w, b=None, relu=False, idx=None, nthreads=0, with_bou
     if rc:
         raise RuntimeError(f"oracle_conv2d_fwd failed ({rc})")
     return (out, bound) if with_bound else out
+
+
+def conv2d_fwd_fused(p: Conv, x, w, alpha=None, beta=None, z=None, relu=False, idx=None,
+                     nthreads=0, with_bound=False):
+    """y = act(alpha[k] * conv + beta[k] + z) in float64 (the layers after a
+    ResNet-50 convolution, Sec. 5.B: batch normalisation folded into
+    (alpha, beta), the tensor add of the residual z). alpha, beta, z may be
+    None; z has y's shape and layout."""
+    lib = _load()
+    x, w = _f64(x), _f64(w)
+    assert x.size == int(np.prod(p.x_shape)) and w.size == int(np.prod(p.w_shape))
+    al = _f64(alpha) if alpha is not None else None
+    be = _f64(beta) if beta is not None else None
+    zz = _f64(z) if z is not None else None
+    if zz is not None:
+        assert zz.size == int(np.prod(p.y_shape))
+    i, n = _idx(idx)
+    out = np.empty(n if i is not None else p.y_shape, dtype=np.float64)
+    bound = np.empty_like(out) if with_bound else None
+    opt = lambda a: _ptr(a, _f64p) if a is not None else None
+    rc = lib.oracle_conv2d_fwd_fused(_ptr(p.d, _i64p), _ptr(x, _f64p), _ptr(w, _f64p), opt(al),
+                                     opt(be), opt(zz), int(bool(relu)),
+                                     _ptr(i, _i64p) if i is not None else None, n,
+                                     _ptr(out, _f64p), _ptr(bound, _f64p) if with_bound else None,
+                                     int(nthreads))
+    if rc:
+        raise RuntimeError(f"oracle_conv2d_fwd_fused failed ({rc})")
+    return (out, bound) if with_bound else out
+
+
+def bn_fold(gamma, bn_beta, mean, var, eps, bias=None):
+    """Inference batch normalisation after a convolution with bias b, folded
+    into the fused forward's per-channel (alpha, beta), in float64."""
+    g, bb, m, v = (_f64(a) for a in (gamma, bn_beta, mean, var))
+    K = g.size
+    b = _f64(bias) if bias is not None else None
+    alpha, beta = np.empty(K), np.empty(K)
+    _load().oracle_bn_fold(K, _ptr(g, _f64p), _ptr(bb, _f64p), _ptr(m, _f64p), _ptr(v, _f64p),
+                           float(eps), _ptr(b, _f64p) if b is not None else None,
+                           _ptr(alpha, _f64p), _ptr(beta, _f64p))
+    return alpha, beta
 
 
 def conv2d_dgrad(p: Conv, g, w, idx=None, nthreads=0, with_bound=False):

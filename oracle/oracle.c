@@ -21,6 +21,21 @@
  *   dw[k,c,r,s] = sum_{n,p,q} g[n,k,p,q] * x[n,c,p*u+r*dh-ph,q*v+s*dw-pw]
  *   db[k]       = sum_{n,p,q} g[n,k,p,q]
  *
+ * The layers around a ResNet-50 convolution (Sec. 5.B: batch normalisation
+ * and tensor additions follow the convolutions) give the fused forward
+ *
+ *   y[n,k,p,q] = act(alpha[k] * conv[n,k,p,q] + beta[k] + z[n,k,p,q])
+ *
+ * (conv the sum above without bias, alpha a per-channel scale, beta a
+ * per-channel shift, z a residual tensor of y's shape, act ReLU or identity),
+ * and inference batch normalisation folded into (alpha, beta):
+ *
+ *   alpha[k] = gamma[k] / sqrt(var[k] + eps)
+ *   beta[k]  = bn_beta[k] + (b[k] - mean[k]) * alpha[k]
+ *
+ * so that alpha*(conv + b) normalised by (mean, var) and shifted by bn_beta
+ * equals alpha*conv + beta.
+ *
  * Every function here is the definition written out as loops in double
  * precision, with the loop order n,k,p,q outside and c,r,s inside. There is
  * no blocking, no im2col and no reordering of the sum. Threads only split the
@@ -171,6 +186,7 @@ static void wgrad_one(const dims_t *D, const double *x, const double *g, int64_t
 typedef struct {
     const dims_t *D;
     const double *a, *b, *bias;
+    const double *alpha, *z;  /* fused forward: per-channel scale, residual (may be NULL) */
     const int64_t *idx;   /* NULL: all outputs 0..count-1 */
     int64_t count;
     int op;               /* 0 fwd, 1 dgrad, 2 wgrad */
@@ -187,9 +203,17 @@ static void do_item(job_t *J, int64_t i) {
         int64_t n, k, p, q;
         y_coords(D, lin, &n, &k, &p, &q);
         fwd_one(D, J->a, J->b, n, k, p, q, &sum, &asum);
+        if (J->alpha) {
+            sum = J->alpha[k] * sum;
+            asum = fabs(J->alpha[k]) * asum;
+        }
         if (J->bias) {
             sum = J->bias[k] + sum;
             asum = fabs(J->bias[k]) + asum;
+        }
+        if (J->z) {
+            sum = sum + J->z[lin];
+            asum = asum + fabs(J->z[lin]);
         }
         if (J->relu && sum < 0.0) sum = 0.0;
     } else if (J->op == 1) {
@@ -252,8 +276,33 @@ int oracle_conv2d_fwd(const int64_t *d, const double *x, const double *w, const 
                       int nthreads) {
     dims_t D;
     if (load_dims(d, &D)) return -1;
-    job_t J = {&D, x, w, bias, idx, idx ? npts : y_count(&D), 0, relu, y, bound, 0, 1};
+    job_t J = {&D, x, w, bias, NULL, NULL, idx, idx ? npts : y_count(&D), 0, relu, y, bound, 0, 1};
     return run(J, nthreads);
+}
+
+/* Fused forward: y = act(alpha[k]*conv + beta[k] + z) at all outputs or at
+ * the npts linear indices idx[]. alpha, beta, z may each be NULL (1, 0, 0); z
+ * has y's shape and layout. bound receives |alpha[k]| sum |x||w| + |beta[k]|
+ * + |z|. */
+int oracle_conv2d_fwd_fused(const int64_t *d, const double *x, const double *w,
+                            const double *alpha, const double *beta, const double *z, int relu,
+                            const int64_t *idx, int64_t npts, double *y, double *bound,
+                            int nthreads) {
+    dims_t D;
+    if (load_dims(d, &D)) return -1;
+    job_t J = {&D, x, w, beta, alpha, z, idx, idx ? npts : y_count(&D), 0, relu, y, bound, 0, 1};
+    return run(J, nthreads);
+}
+
+/* Inference batch normalisation folded into a per-channel scale and shift
+ * (see the header); bias may be NULL (0). */
+void oracle_bn_fold(int64_t K, const double *gamma, const double *bn_beta, const double *mean,
+                    const double *var, double eps, const double *bias, double *alpha,
+                    double *beta) {
+    for (int64_t k = 0; k < K; ++k) {
+        alpha[k] = gamma[k] / sqrt(var[k] + eps);
+        beta[k] = bn_beta[k] + ((bias ? bias[k] : 0.0) - mean[k]) * alpha[k];
+    }
 }
 
 /* dx over all inputs or at npts linear x indices. */
@@ -261,7 +310,7 @@ int oracle_conv2d_dgrad(const int64_t *d, const double *g, const double *w, cons
                         int64_t npts, double *dx, double *bound, int nthreads) {
     dims_t D;
     if (load_dims(d, &D)) return -1;
-    job_t J = {&D, g, w, NULL, idx, idx ? npts : x_count(&D), 1, 0, dx, bound, 0, 1};
+    job_t J = {&D, g, w, NULL, NULL, NULL, idx, idx ? npts : x_count(&D), 1, 0, dx, bound, 0, 1};
     return run(J, nthreads);
 }
 
@@ -270,7 +319,7 @@ int oracle_conv2d_wgrad(const int64_t *d, const double *x, const double *g, cons
                         int64_t npts, double *dw, double *bound, int nthreads) {
     dims_t D;
     if (load_dims(d, &D)) return -1;
-    job_t J = {&D, x, g, NULL, idx, idx ? npts : w_count(&D), 2, 0, dw, bound, 0, 1};
+    job_t J = {&D, x, g, NULL, NULL, NULL, idx, idx ? npts : w_count(&D), 2, 0, dw, bound, 0, 1};
     return run(J, nthreads);
 }
 

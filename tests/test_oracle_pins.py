@@ -372,3 +372,78 @@ def test_scale_quant_definition():
     deq = vals * scales[:, None]
     big = np.abs(a) > scales[:, None] * 2.0 ** -6 * 4
     assert np.all(np.abs(deq - a)[big] <= np.abs(a)[big] * 2.0 ** -4 * (1 + 1e-6))
+
+
+# ---- fused forward (batch normalisation folded, residual add, ReLU) ----
+
+@pytest.mark.parametrize("case", CASES[:6])
+@pytest.mark.parametrize("relu", [False, True])
+def test_fused_bn_residual_matches_torch_library(case, relu):
+    """conv + bias -> inference batch_norm -> + residual -> ReLU with PyTorch's
+    own float64 conv2d and batch_norm equals the oracle's fused forward with
+    the folded (alpha, beta): pins the fold formula, where alpha and beta enter,
+    the residual's indexing and the activation."""
+    N, C, H, W, K, R, S, st, pd, dl = case
+    p = Conv(N, C, H, W, K, R, S, st, pd, dl, "NCHW")
+    r = _rng(11)
+    x = r.normal(size=(N, C, H, W))
+    w = r.normal(size=(K, C, R, S))
+    b = r.normal(size=K)
+    gamma, bn_beta = r.uniform(0.5, 1.5, K), r.normal(size=K)
+    mean, var, eps = r.normal(size=K), r.uniform(0.2, 2.0, K), 1e-5
+    z = r.normal(size=p.y_shape)
+    T = torch.from_numpy
+    ref = torch.nn.functional.conv2d(T(x), T(w), T(b), stride=st, padding=pd, dilation=dl)
+    ref = torch.nn.functional.batch_norm(ref, T(mean), T(var), T(gamma), T(bn_beta),
+                                         training=False, eps=eps) + T(z)
+    if relu:
+        ref = torch.relu(ref)
+    alpha, beta = oracle.bn_fold(gamma, bn_beta, mean, var, eps, bias=b)
+    y = oracle.conv2d_fwd_fused(p, x, w, alpha, beta, z, relu=relu)
+    assert np.max(np.abs(y - ref.numpy())) < 1e-10
+
+
+@pytest.mark.parametrize("layout", ["NCHW", "NHWC"])
+def test_fused_defaults_reduce_to_plain_forward(layout):
+    p = Conv(2, 3, 7, 6, 4, 3, 3, (1, 1), (1, 1), (1, 1), layout)
+    r = _rng(12)
+    x, w, b = r.normal(size=p.x_shape), r.normal(size=p.w_shape), r.normal(size=4)
+    y0, b0 = oracle.conv2d_fwd(p, x, w, b, relu=True, with_bound=True)
+    y1, b1 = oracle.conv2d_fwd_fused(p, x, w, None, b, None, relu=True, with_bound=True)
+    assert np.array_equal(y0, y1) and np.array_equal(b0, b1)
+
+
+@pytest.mark.parametrize("layout", ["NCHW", "NHWC"])
+def test_fused_integer_residual_and_power_of_two_scale_exact(layout):
+    """Integer operands, alpha a power of two: every step is exact in FP64, so
+    y = 4*conv + beta + z holds bit for bit, and the bound adds |alpha|, |beta|
+    and |z| the same way."""
+    p = Conv(2, 4, 6, 7, 3, 3, 3, (2, 1), (1, 1), (1, 1), layout)
+    r = _rng(13)
+    x = r.integers(-4, 5, p.x_shape).astype(float)
+    w = r.integers(-4, 5, p.w_shape).astype(float)
+    beta = r.integers(-8, 9, 3).astype(float)
+    z = r.integers(-16, 17, p.y_shape).astype(float)
+    alpha = np.full(3, -4.0)
+    y, bound = oracle.conv2d_fwd_fused(p, x, w, alpha, beta, z, with_bound=True)
+    c, cb = oracle.conv2d_fwd(p, x, w, None, with_bound=True)
+    kax = 1 if layout == "NCHW" else 3
+    shape = [1, 1, 1, 1]
+    shape[kax] = 3
+    assert np.array_equal(y, -4.0 * c + beta.reshape(shape) + z)
+    assert np.array_equal(bound, 4.0 * cb + np.abs(beta).reshape(shape) + np.abs(z))
+
+
+def test_bn_fold_definition():
+    """alpha*(conv + b) normalised and shifted equals alpha*conv + beta for any
+    conv value: checked at random points against the unfolded formula."""
+    r = _rng(14)
+    K = 9
+    gamma, bn_beta, b = r.normal(size=K), r.normal(size=K), r.normal(size=K)
+    mean, var, eps = r.normal(size=K), r.uniform(0.1, 3, K), 1e-3
+    alpha, beta = oracle.bn_fold(gamma, bn_beta, mean, var, eps, bias=b)
+    for v in r.normal(size=5) * 10:
+        unfolded = (v + b - mean) / np.sqrt(var + eps) * gamma + bn_beta
+        assert np.max(np.abs(alpha * v + beta - unfolded)) < 1e-12
+    a0, b0 = oracle.bn_fold(gamma, bn_beta, mean, var, eps)
+    assert np.allclose(b0, bn_beta - mean * a0, rtol=0, atol=1e-15)
