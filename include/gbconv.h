@@ -134,6 +134,42 @@ gbconv_status_t conv2d_fwd(const gbconv_problem_t *prob, const void *x, const vo
                            const float *bias, const float *x_scale, const float *w_scale,
                            void *y, void *ws, size_t ws_bytes, gbconv_stream_t stream);
 
+/* Forward with the layers that follow a ResNet-50 convolution fused into the
+ * epilogue (paper Sec. 5.B: the model's convolutions are followed by batch
+ * normalisation and tensor additions):
+ *
+ *   y[n,p,q,k] = act(scale[k] * conv(x, w)[n,p,q,k] + bias[k] + residual[n,p,q,k])
+ *
+ * conv(x, w) is the convolution of conv2d_fwd without its bias (for E4M3
+ * inputs already multiplied by x_scale * w_scale[k]); act is ReLU when
+ * GBCONV_FLAG_RELU is set. Inference batch normalisation folds into (scale,
+ * bias): see gbconv_bn_fold.
+ *   prob, x, w, x_scale, w_scale, y, ws, ws_bytes, stream: as in conv2d_fwd
+ *   bias     [K] fp32, read when GBCONV_FLAG_BIAS is set (the shift)
+ *   scale    [K] fp32 device pointer, or NULL for 1
+ *   residual y's shape, layout and out_dtype, or NULL for 0. It may be y
+ *            itself (in-place add: each element is read before it is
+ *            written, by the same thread) but not x or w. Tensor-core paths
+ *            require it 16-byte aligned (else GBCONV_ERR_ALIGNMENT).
+ * Arithmetic: FP32, in the order scale, bias, residual, activation, then one
+ * rounding to out_dtype. Not available through conv2d_grouped. */
+gbconv_status_t conv2d_fwd_fused(const gbconv_problem_t *prob, const void *x, const void *w,
+                                 const float *bias, const float *scale, const void *residual,
+                                 const float *x_scale, const float *w_scale, void *y, void *ws,
+                                 size_t ws_bytes, gbconv_stream_t stream);
+
+/* Inference batch normalisation of a convolution with bias b, folded into
+ * conv2d_fwd_fused's per-channel scale and shift (paper Sec. 5.B, the batch
+ * normalisation layers of ResNet-50):
+ *   scale[k] = gamma[k] / sqrt(var[k] + eps)
+ *   shift[k] = bn_beta[k] + (b[k] - mean[k]) * scale[k]
+ * All arrays are K fp32 device pointers; bias may be NULL (b = 0). FP32 with
+ * correctly rounded square root and division. Asynchronous on stream;
+ * GBCONV_ERR_INVALID_ARG for K < 0, a NULL required pointer or eps < 0 (or NaN). */
+gbconv_status_t gbconv_bn_fold(int32_t K, const float *gamma, const float *bn_beta,
+                               const float *mean, const float *var, float eps, const float *bias,
+                               float *scale, float *shift, gbconv_stream_t stream);
+
 /* Data gradient (paper Sec. 5.B, backward pass; the transposed convolution).
  *   dy [N,P,Q,K] or [N,K,P,Q] (in_dtype), w as in conv2d_fwd (in_dtype),
  *   dx [N,H,W,C] or [N,C,H,W] (out_dtype). dx is fully overwritten.

@@ -34,7 +34,7 @@ EXPORTS = [
     "conv2d_wgrad", "conv2d_grouped", "gbconv_quantize_e4m3", "gbconv_get_config",
     "gbconv_set_config", "gbconv_tune", "gbconv_tune_cache_save", "gbconv_tune_cache_load",
     "gbconv_get_device_error", "gbconv_status_string", "gbconv_debug_set", "gbconv_version",
-    "gbconv_shutdown", "conv2d_dgrad_noalloc",
+    "gbconv_shutdown", "conv2d_dgrad_noalloc", "conv2d_fwd_fused", "gbconv_bn_fold",
 ]
 
 
@@ -88,6 +88,10 @@ _SIGS = {
     "gbconv_version": (ctypes.c_int32, []),
     "gbconv_shutdown": (None, []),
     "conv2d_dgrad_noalloc": (ctypes.c_int, [_PROB, _P, _P, _P, _P]),
+    "conv2d_fwd_fused": (ctypes.c_int, [_PROB, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                        ctypes.c_size_t, _P]),
+    "gbconv_bn_fold": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, ctypes.c_float, _P, _P, _P,
+                                      _P]),
 }
 
 
@@ -152,6 +156,18 @@ def gbconv_workspace_size(op, prob):
 def conv2d_fwd(prob, x, w, bias, x_scale, w_scale, y, ws, ws_bytes, stream):
     return lib().conv2d_fwd(ctypes.byref(prob), _vp(x), _vp(w), _vp(bias), _vp(x_scale),
                             _vp(w_scale), _vp(y), _vp(ws), ws_bytes, _vp(stream))
+
+
+def conv2d_fwd_fused(prob, x, w, bias, scale, residual, x_scale, w_scale, y, ws, ws_bytes,
+                     stream):
+    return lib().conv2d_fwd_fused(ctypes.byref(prob), _vp(x), _vp(w), _vp(bias), _vp(scale),
+                                  _vp(residual), _vp(x_scale), _vp(w_scale), _vp(y), _vp(ws),
+                                  ws_bytes, _vp(stream))
+
+
+def gbconv_bn_fold(K, gamma, bn_beta, mean, var, eps, bias, scale, shift, stream):
+    return lib().gbconv_bn_fold(int(K), _vp(gamma), _vp(bn_beta), _vp(mean), _vp(var),
+                                float(eps), _vp(bias), _vp(scale), _vp(shift), _vp(stream))
 
 
 def conv2d_dgrad(prob, dy, w, dx, ws, ws_bytes, stream):

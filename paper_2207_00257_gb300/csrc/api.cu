@@ -199,17 +199,18 @@ size_t wgrad_ws_bytes(const Dims &d, int slices) {
 
 gbconv_status_t do_fwd(const Dims &d, const TcConfig &cfg, const void *x, const void *w,
                        const float *bias, const float *x_scale, const float *w_scale, void *y,
-                       cudaStream_t st) {
+                       cudaStream_t st, const Fused &fz = Fused{}) {
     if (d.M() == 0) return GBCONV_OK;
     if (d.in_dtype == GBCONV_F32) {
         if (d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
-        return launch_simt_fwd(d, x, w, bias, y, st);
+        return launch_simt_fwd(d, x, w, bias, y, st, fz);
     }
     if (d.layout != GBCONV_NHWC) return GBCONV_ERR_UNSUPPORTED;
     if (d.in_dtype == GBCONV_E4M3 && (!x_scale || !w_scale)) return GBCONV_ERR_INVALID_ARG;
     gbconv_status_t s = check_tc_fwd(d, x, w, y);
     if (s != GBCONV_OK) return s;
-    return launch_tc_fwd(d, cfg, x, w, bias, x_scale, w_scale, y, st);
+    if (fz.z && !aligned16(fz.z)) return GBCONV_ERR_ALIGNMENT;  // 16-byte residual loads
+    return launch_tc_fwd(d, cfg, x, w, bias, x_scale, w_scale, y, st, fz);
 }
 
 gbconv_status_t do_dgrad(const Dims &d, const TcConfig &cfg, const void *dy, const void *w,
@@ -339,6 +340,36 @@ gbconv_status_t conv2d_fwd(const gbconv_problem_t *prob, const void *x, const vo
     if (x == y || w == y) return GBCONV_ERR_INVALID_ARG;
     return do_fwd(d, config_for(GBCONV_OP_FWD, *prob, d), x, w, bias, x_scale, w_scale, y,
                   static_cast<cudaStream_t>(stream));
+}
+
+gbconv_status_t conv2d_fwd_fused(const gbconv_problem_t *prob, const void *x, const void *w,
+                                 const float *bias, const float *scale, const void *residual,
+                                 const float *x_scale, const float *w_scale, void *y, void *ws,
+                                 size_t ws_bytes, gbconv_stream_t stream) {
+    (void)ws;
+    (void)ws_bytes;
+    Dims d;
+    gbconv_status_t s = make_dims(prob, &d);
+    if (s != GBCONV_OK) return s;
+    if (d.N == 0) return GBCONV_OK;
+    if (!x || !w || !y || ((d.flags & GBCONV_FLAG_BIAS) && !bias)) return GBCONV_ERR_INVALID_ARG;
+    if (x == y || w == y || residual == x || residual == w) return GBCONV_ERR_INVALID_ARG;
+    Fused fz;
+    fz.alpha = scale;
+    fz.z = residual;
+    return do_fwd(d, config_for(GBCONV_OP_FWD, *prob, d), x, w, bias, x_scale, w_scale, y,
+                  static_cast<cudaStream_t>(stream), fz);
+}
+
+gbconv_status_t gbconv_bn_fold(int32_t K, const float *gamma, const float *bn_beta,
+                               const float *mean, const float *var, float eps, const float *bias,
+                               float *scale, float *shift, gbconv_stream_t stream) {
+    if (K < 0) return GBCONV_ERR_INVALID_ARG;
+    if (K == 0) return GBCONV_OK;
+    if (!gamma || !bn_beta || !mean || !var || !scale || !shift || !(eps >= 0.f))
+        return GBCONV_ERR_INVALID_ARG;
+    return launch_bn_fold(K, gamma, bn_beta, mean, var, eps, bias, scale, shift,
+                          static_cast<cudaStream_t>(stream));
 }
 
 gbconv_status_t conv2d_dgrad(const gbconv_problem_t *prob, const void *dy, const void *w,

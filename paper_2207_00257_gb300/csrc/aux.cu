@@ -142,6 +142,23 @@ __global__ void transpose_krsc(const T *__restrict__ w, T *__restrict__ wt, int 
     }
 }
 
+// Inference batch normalisation after a convolution with bias, folded into
+// the fused forward's per-channel scale and shift (sqrtf and the division
+// are the correctly rounded FP32 operations).
+__global__ void bn_fold_kernel(int K, const float *__restrict__ gamma,
+                               const float *__restrict__ bn_beta, const float *__restrict__ mean,
+                               const float *__restrict__ var, float eps,
+                               const float *__restrict__ bias, float *__restrict__ scale,
+                               float *__restrict__ shift) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const float a = gamma[k] / sqrtf(var[k] + eps);
+    scale[k] = a;
+    shift[k] = bn_beta[k] + ((bias ? bias[k] : 0.f) - mean[k]) * a;
+}
+
 // Zeroes the positions (n, u*h' + a, v*w' + b, :) of an NHWC tensor: a
 // sub-pixel phase of the data gradient that no filter tap reaches.
 template <typename T>
@@ -322,6 +339,13 @@ gbconv_status_t launch_transpose_filter(const Dims &d, const void *w, void *wt, 
     return cuda_status(launch_pdl(transpose_krsc<__nv_bfloat16>, dim3(g), dim3(256), 0, st,
                                   (const __nv_bfloat16 *)w, (__nv_bfloat16 *)wt, d.K, d.R * d.S,
                                   d.C));
+}
+
+gbconv_status_t launch_bn_fold(int K, const float *gamma, const float *bn_beta, const float *mean,
+                               const float *var, float eps, const float *bias, float *scale,
+                               float *shift, cudaStream_t st) {
+    return cuda_status(launch_pdl(bn_fold_kernel, dim3((K + 255) / 256), dim3(256), 0, st, K, gamma,
+                                  bn_beta, mean, var, eps, bias, scale, shift));
 }
 
 gbconv_status_t launch_zero_phase(const Dims &d, void *dx, int a, int b, cudaStream_t st) {

@@ -30,6 +30,10 @@ struct EpiArgs {
     int relu, out_f32;
     const float *bias;     // [K] or null
     const float *w_scale;  // [K] FP8 per-channel scales (FP8 only)
+    const float *alpha;    // [K] fused per-channel scale (folded batch norm) or null
+    const void *z;         // fused residual, y's shape and dtype (may be y) or null
+    long long M;           // rows of y as [M][K] (2-D stores)
+    int Q;                 // row length of y as [N*P][Q][K] (3-D stores)
 };
 
 __device__ __forceinline__ void store_chunk(const CUtensorMap *map, const void *src, int c0, int c1,
@@ -54,22 +58,73 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 //                unit c ^ ((r >> 1) & 3)), NBUF 2 KB buffers used in turn;
 //   FP32 output: 32 rows x 128 B, 128-byte swizzle (unit c ^ (r & 7)), NBUF/2
 //                4 KB buffers used in turn.
-template <bool FP8, int NBUF>
+// Residual values of this lane's row, columns col0 .. col0+31 (0 outside y).
+__device__ __forceinline__ void load_residual(const EpiArgs &pa, int col0, int c1, int c2,
+                                              int lane, float (&zr)[32]) {
+    long long row;
+    bool valid;
+    if (c2 < 0) {
+        row = (long long)c1 + lane;
+        valid = row < pa.M;
+    } else {
+        row = (long long)c2 * pa.Q + c1 + lane;
+        valid = c1 + lane < pa.Q;
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {  // 8 channels per 16-byte (BF16) or 32-byte (FP32) group
+        const int c = col0 + 8 * g;
+        const bool ok = valid && c < pa.K;  // K is a multiple of 8
+        if (pa.out_f32) {
+            const float4 *p = reinterpret_cast<const float4 *>(
+                static_cast<const float *>(pa.z) + (ok ? row * pa.K + c : 0));
+            const float4 a = ok ? p[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 b = ok ? p[1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            zr[8 * g + 0] = a.x; zr[8 * g + 1] = a.y; zr[8 * g + 2] = a.z; zr[8 * g + 3] = a.w;
+            zr[8 * g + 4] = b.x; zr[8 * g + 5] = b.y; zr[8 * g + 6] = b.z; zr[8 * g + 7] = b.w;
+        } else {
+            const uint4 u = ok ? *reinterpret_cast<const uint4 *>(
+                                     static_cast<const __nv_bfloat16 *>(pa.z) + row * pa.K + c)
+                               : make_uint4(0, 0, 0, 0);
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 f = __bfloat1622float2(h[i]);
+                zr[8 * g + 2 * i] = f.x;
+                zr[8 * g + 2 * i + 1] = f.y;
+            }
+        }
+    }
+}
+
+// FUSED instantiations also apply the per-channel scale and the residual
+// (EpiArgs::alpha, EpiArgs::z); the others ignore both fields.
+template <bool FP8, int NBUF, bool FUSED = false>
 __device__ __forceinline__ void epilogue_chunk(const uint32_t (&v)[32], const EpiArgs &pa,
                                                const CUtensorMap *tmY, float xs, int col0,
                                                int c1, int c2, int lane, uint8_t *sbuf, int &ebuf) {
-    float scl = 1.f, bl = 0.f;
+    float scl = 1.f, bl = 0.f, al = 1.f;
     const int mycol = col0 + lane;
     if (mycol < pa.K) {
         if (FP8) scl = xs * __ldg(pa.w_scale + mycol);
         if (pa.bias) bl = __ldg(pa.bias + mycol);
+        if (FUSED && pa.alpha) al = __ldg(pa.alpha + mycol);
+    }
+    float zr[FUSED ? 32 : 1];
+    if constexpr (FUSED) {
+        if (pa.z) load_residual(pa, col0, c1, c2, lane, zr);
     }
     float f[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
         float a = __uint_as_float(v[i]);
         if (FP8) a = a * __shfl_sync(0xffffffffu, scl, i);
+        if constexpr (FUSED) {
+            if (pa.alpha) a = a * __shfl_sync(0xffffffffu, al, i);
+        }
         if (pa.bias) a = a + __shfl_sync(0xffffffffu, bl, i);
+        if constexpr (FUSED) {
+            if (pa.z) a = a + zr[i];
+        }
         if (pa.relu) a = fmaxf(a, 0.f);
         f[i] = a;
     }

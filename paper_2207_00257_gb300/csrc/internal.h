@@ -28,6 +28,14 @@ struct Guard {
     int skip_loads;      // test control: issue no loads (consumers then time out)
 };
 
+// Fused forward epilogue (batch normalisation folded, residual add): y =
+// act(alpha[k]*conv + bias[k] + z). alpha [K] fp32 and z (y's shape, layout
+// and dtype; may be y itself) are optional.
+struct Fused {
+    const float *alpha = nullptr;
+    const void *z = nullptr;
+};
+
 // Error codes written to the device error word.
 enum : unsigned { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1 };
 
@@ -38,7 +46,7 @@ gbconv_status_t cuda_status(cudaError_t e);
 
 // simt.cu: CUDA-core FP32-accumulate kernels (any layout/stride/dilation).
 gbconv_status_t launch_simt_fwd(const Dims &d, const void *x, const void *w, const float *bias,
-                                void *y, cudaStream_t st);
+                                void *y, cudaStream_t st, const Fused &fz = Fused{});
 gbconv_status_t launch_simt_dgrad(const Dims &d, const void *g, const void *w, void *dx,
                                   cudaStream_t st);
 // Partial sums of dw per slice: ws[slice][K*C*R*S] in the filter layout.
@@ -53,6 +61,10 @@ gbconv_status_t launch_bias_grad(const Dims &d, const void *g, float *db, float 
 gbconv_status_t launch_rotate_filter(const Dims &d, const void *w, void *w_rot, cudaStream_t st);
 // w[k][r][s][c] -> wT[c][r][s][k] (BF16)
 gbconv_status_t launch_transpose_filter(const Dims &d, const void *w, void *wt, cudaStream_t st);
+// scale = gamma / sqrt(var + eps), shift = bn_beta + (bias - mean) * scale
+gbconv_status_t launch_bn_fold(int K, const float *gamma, const float *bn_beta, const float *mean,
+                               const float *var, float eps, const float *bias, float *scale,
+                               float *shift, cudaStream_t st);
 // zeroes dx at rows u*h' + a, columns v*w' + b (NHWC, out_dtype of d)
 gbconv_status_t launch_zero_phase(const Dims &d, void *dx, int a, int b, cudaStream_t st);
 gbconv_status_t launch_quantize_e4m3(const void *in, int in_dtype, long long rows, long long len,
@@ -70,13 +82,14 @@ bool tc_fwd_supported(const Dims &d);
 TcConfig tc_fwd_default_config(const Dims &d);
 gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg, const void *x, const void *w,
                               const float *bias, const float *x_scale, const float *w_scale,
-                              void *y, cudaStream_t st);
+                              void *y, cudaStream_t st, const Fused &fz = Fused{});
 // tc_fwd_shift.cu: stride-1 layers, one input band per channel block.
 bool tc_fwd_shift_supported(const Dims &d, int block_n);
 bool tc_fwd_shift_preferred(const Dims &d, int block_n);  // automatic choice
 gbconv_status_t launch_tc_fwd_shift(const Dims &d, const TcConfig &cfg, const void *x,
                                     const void *w, const float *bias, const float *x_scale,
-                                    const float *w_scale, void *y, cudaStream_t st);
+                                    const float *w_scale, void *y, cudaStream_t st,
+                                    const Fused &fz = Fused{});
 // tc_fwd_t.cu: band kernel with output channels on the MMA's M (strides by
 // phase decomposition; 1x1 stride-1 layers as a flat GEMM), and the data
 // gradient of strided layers by sub-pixel phases on the same kernel.
@@ -86,7 +99,7 @@ gbconv_status_t launch_tc_dgrad_t(const Dims &d, const void *dy, const void *wT,
 int tc_fwd_t_tile(const Dims &d);  // output-channel tile (64 / 128), 0 if unsuitable
 gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, const float *bias,
                                 const float *x_scale, const float *w_scale, void *y,
-                                cudaStream_t st);
+                                cudaStream_t st, const Fused &fz = Fused{});
 gbconv_status_t launch_tc_grouped(int count, const Dims *d, const TcConfig *cfg,
                                   const void *const *x, const void *const *w,
                                   const float *const *bias, void *const *y, cudaStream_t st);

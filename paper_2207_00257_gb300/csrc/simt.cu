@@ -32,6 +32,9 @@ template <>
 __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16 *p) {
     return __bfloat162float(*p);
 }
+// Coherent load (the residual may be the output tensor itself).
+__device__ __forceinline__ float ldz(const float *p) { return *p; }
+__device__ __forceinline__ float ldz(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 template <typename T>
 __device__ __forceinline__ void stf(T *p, float v);
 template <>
@@ -138,6 +141,8 @@ struct FwdLoader {
     To *y;
     int relu;
     int cb;  // channel blocks of 16
+    const float *alpha;  // fused: per-channel scale (may be null)
+    const To *z;         // fused: residual of y's shape and layout (may be null)
     // per-thread state
     int m0, n0, t;
     long long xb[8];
@@ -219,9 +224,11 @@ struct FwdLoader {
                 int k = n0 + tn * 4 + j;
                 if (k >= d.K) continue;
                 float v = acc[i][j];
-                if (bias) v = bias[k] + v;
-                if (relu) v = fmaxf(v, 0.f);
                 long long off = NHWC ? m * d.K + k : (((long long)n * d.K + k) * d.P + p) * d.Q + q;
+                if (alpha) v = v * alpha[k];
+                if (bias) v = bias[k] + v;
+                if (z) v = v + ldz(z + off);
+                if (relu) v = fmaxf(v, 0.f);
                 stf(y + off, v);
             }
         }
@@ -430,17 +437,19 @@ gbconv_status_t launch(const L &ldr, dim3 grid, cudaStream_t st) {
 
 template <typename Ti, typename To>
 gbconv_status_t fwd_typed(const Dims &d, const void *x, const void *w, const float *bias, void *y,
-                          cudaStream_t st) {
+                          cudaStream_t st, const Fused &fz) {
     long long M = d.M();
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((d.K + BN - 1) / BN), 1);
     int relu = (d.flags & GBCONV_FLAG_RELU) ? 1 : 0;
     const float *b = (d.flags & GBCONV_FLAG_BIAS) ? bias : nullptr;
     int cb = (d.C + BK - 1) / BK;
     if (d.layout == GBCONV_NHWC) {
-        FwdLoader<Ti, To, true> L{to_k(d), (const Ti *)x, (const Ti *)w, b, (To *)y, relu, cb};
+        FwdLoader<Ti, To, true> L{to_k(d), (const Ti *)x, (const Ti *)w, b, (To *)y, relu, cb,
+                                  fz.alpha, (const To *)fz.z};
         return launch(L, grid, st);
     }
-    FwdLoader<Ti, To, false> L{to_k(d), (const Ti *)x, (const Ti *)w, b, (To *)y, relu, cb};
+    FwdLoader<Ti, To, false> L{to_k(d), (const Ti *)x, (const Ti *)w, b, (To *)y, relu, cb,
+                               fz.alpha, (const To *)fz.z};
     return launch(L, grid, st);
 }
 
@@ -475,13 +484,13 @@ gbconv_status_t wgrad_typed(const Dims &d, const void *x, const void *g, float *
 }  // namespace
 
 gbconv_status_t launch_simt_fwd(const Dims &d, const void *x, const void *w, const float *bias,
-                                void *y, cudaStream_t st) {
+                                void *y, cudaStream_t st, const Fused &fz) {
     if (d.in_dtype == GBCONV_F32 && d.out_dtype == GBCONV_F32)
-        return fwd_typed<float, float>(d, x, w, bias, y, st);
+        return fwd_typed<float, float>(d, x, w, bias, y, st, fz);
     if (d.in_dtype == GBCONV_BF16 && d.out_dtype == GBCONV_F32)
-        return fwd_typed<__nv_bfloat16, float>(d, x, w, bias, y, st);
+        return fwd_typed<__nv_bfloat16, float>(d, x, w, bias, y, st, fz);
     if (d.in_dtype == GBCONV_BF16 && d.out_dtype == GBCONV_BF16)
-        return fwd_typed<__nv_bfloat16, __nv_bfloat16>(d, x, w, bias, y, st);
+        return fwd_typed<__nv_bfloat16, __nv_bfloat16>(d, x, w, bias, y, st, fz);
     return GBCONV_ERR_UNSUPPORTED;
 }
 

@@ -72,6 +72,8 @@ struct FwdParams {
     int num_tiles;
     int stages;
     int raster;
+    const float *alpha;  // fused epilogue of a single problem (G == 1): per-channel scale
+    const void *z;       // and residual; null otherwise
     Guard guard;
 };
 
@@ -104,7 +106,9 @@ __device__ __forceinline__ void decode(const FwdParams<G> &prm, int tile, int &g
     }
 }
 
-template <int BN, bool FP8, int G>
+// FUSED: the epilogue also applies the per-channel scale and the residual
+// (single-problem launches only).
+template <int BN, bool FP8, int G, bool FUSED = false>
 __global__ void __launch_bounds__(EpiShape<BN>::threads, 1) tc_fwd_kernel(const __grid_constant__ FwdParams<G> prm) {
     constexpr int EPI_WARPS = EpiShape<BN>::warps;
     constexpr int EPI_BYTES = EpiShape<BN>::warp_bytes;
@@ -327,7 +331,10 @@ __global__ void __launch_bounds__(EpiShape<BN>::threads, 1) tc_fwd_kernel(const 
                 }
                 const int col0 = nt * pa.bn + j * 32;
                 if (col0 >= pa.K || row0 >= pa.M) continue;  // chunk entirely outside y
-                epilogue_chunk<FP8, EpiShape<BN>::nbuf>(v, EpiArgs{pa.K, pa.relu, pa.out_f32, pa.bias, pa.w_scale},
+                epilogue_chunk<FP8, EpiShape<BN>::nbuf, FUSED>(v, EpiArgs{pa.K, pa.relu, pa.out_f32, pa.bias, pa.w_scale,
+                                                                    G == 1 ? prm.alpha : nullptr,
+                                                                    G == 1 ? prm.z : nullptr,
+                                                                    (long long)pa.M, pa.Q},
                                     &prm.tmY[g], xs, col0, row0, -1, lane, sbuf, ebuf);
             }
             if (!released) {
@@ -363,17 +370,24 @@ size_t smem_bytes(int bn, int stages) {
     return (size_t)SMEM_ALIGN + (size_t)stages * (A_BYTES + bn * 128) + EPI_TOTAL + BAR_BYTES;
 }
 
-template <int BN, bool FP8, int G>
+template <int BN, bool FP8, int G, bool FUSED = false>
 gbconv_status_t launch_kernel(const FwdParams<G> &prm, int grid, cudaStream_t st) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(tc_fwd_kernel<BN, FP8, G>,
+        attr_err = cudaFuncSetAttribute(tc_fwd_kernel<BN, FP8, G, FUSED>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     });
     if (attr_err != cudaSuccess) return cuda_status(attr_err);
     size_t smem = smem_bytes(BN, prm.stages);
-    return cuda_status(launch_pdl(tc_fwd_kernel<BN, FP8, G>, dim3(grid), dim3(EpiShape<BN>::threads), smem, st, prm));
+    return cuda_status(launch_pdl(tc_fwd_kernel<BN, FP8, G, FUSED>, dim3(grid),
+                                  dim3(EpiShape<BN>::threads), smem, st, prm));
+}
+
+template <int BN, bool FUSED>
+gbconv_status_t launch_single(const FwdParams<1> &prm, bool fp8, int grid, cudaStream_t st) {
+    return fp8 ? launch_kernel<BN, true, 1, FUSED>(prm, grid, st)
+               : launch_kernel<BN, false, 1, FUSED>(prm, grid, st);
 }
 
 // Fills pa, tmA, tmB for one problem; bn is the tile width used.
@@ -481,7 +495,7 @@ TcConfig tc_fwd_default_config(const Dims &d) {
 
 gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void *x,
                               const void *w, const float *bias, const float *x_scale,
-                              const float *w_scale, void *y, cudaStream_t st) {
+                              const float *w_scale, void *y, cudaStream_t st, const Fused &fz) {
     TcConfig cfg = cfg_in;
     if (cfg.block_n != 32 && cfg.block_n != 64 && cfg.block_n != 128 && cfg.block_n != 256)
         return GBCONV_ERR_INVALID_ARG;
@@ -493,13 +507,13 @@ gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void 
     // spare columns.
     if (cfg.algo == GBCONV_ALGO_SHIFT_T || (cfg.algo == GBCONV_ALGO_AUTO && d.R * d.S > 1)) {
         if (tc_fwd_t_tile(d))
-            return launch_tc_fwd_t(d, x, w, bias, x_scale, w_scale, y, st);
+            return launch_tc_fwd_t(d, x, w, bias, x_scale, w_scale, y, st, fz);
         if (cfg.algo == GBCONV_ALGO_SHIFT_T) return GBCONV_ERR_UNSUPPORTED;
     }
     if (cfg.algo == GBCONV_ALGO_SHIFT && tc_fwd_shift_supported(d, cfg.block_n))
-        return launch_tc_fwd_shift(d, cfg, x, w, bias, x_scale, w_scale, y, st);
+        return launch_tc_fwd_shift(d, cfg, x, w, bias, x_scale, w_scale, y, st, fz);
     if (cfg.algo == GBCONV_ALGO_AUTO && d.R * d.S > 1 && tc_fwd_shift_preferred(d, cfg.block_n))
-        return launch_tc_fwd_shift(d, cfg, x, w, bias, x_scale, w_scale, y, st);
+        return launch_tc_fwd_shift(d, cfg, x, w, bias, x_scale, w_scale, y, st, fz);
     if (cfg.algo == GBCONV_ALGO_SHIFT) return GBCONV_ERR_UNSUPPORTED;  // not a stride-1 band layer
     if (cfg.stages < 2 || cfg.stages > max_stages(cfg.block_n)) cfg.stages = max_stages(cfg.block_n);
     if (d.M() == 0) return GBCONV_OK;
@@ -514,15 +528,25 @@ gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void 
     prm.tile_start[1] = prm.num_tiles;
     prm.stages = cfg.stages;
     prm.raster = cfg.raster;
+    prm.alpha = fz.alpha;
+    prm.z = fz.z;
     prm.guard = make_guard();
     if (!prm.guard.err) return GBCONV_ERR_CUDA;
     int grid = std::min(prm.num_tiles, sm_count());
     const bool fp8 = d.in_dtype == GBCONV_E4M3;
+    if (fz.alpha || fz.z) {
+        switch (cfg.block_n) {
+            case 32: return launch_single<32, true>(prm, fp8, grid, st);
+            case 64: return launch_single<64, true>(prm, fp8, grid, st);
+            case 128: return launch_single<128, true>(prm, fp8, grid, st);
+            default: return launch_single<256, true>(prm, fp8, grid, st);
+        }
+    }
     switch (cfg.block_n) {
-        case 32: return fp8 ? launch_kernel<32, true, 1>(prm, grid, st) : launch_kernel<32, false, 1>(prm, grid, st);
-        case 64: return fp8 ? launch_kernel<64, true, 1>(prm, grid, st) : launch_kernel<64, false, 1>(prm, grid, st);
-        case 128: return fp8 ? launch_kernel<128, true, 1>(prm, grid, st) : launch_kernel<128, false, 1>(prm, grid, st);
-        default: return fp8 ? launch_kernel<256, true, 1>(prm, grid, st) : launch_kernel<256, false, 1>(prm, grid, st);
+        case 32: return launch_single<32, false>(prm, fp8, grid, st);
+        case 64: return launch_single<64, false>(prm, fp8, grid, st);
+        case 128: return launch_single<128, false>(prm, fp8, grid, st);
+        default: return launch_single<256, false>(prm, fp8, grid, st);
     }
 }
 

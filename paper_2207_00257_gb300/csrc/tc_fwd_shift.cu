@@ -76,7 +76,8 @@ __device__ __forceinline__ void sdecode(const ShiftParams &p, int tile, int &n, 
     p0 = (mt - n * p.p_tiles) * p.TR;
 }
 
-template <int BN, bool FP8>
+// FUSED: the epilogue also applies the per-channel scale and the residual.
+template <int BN, bool FP8, bool FUSED>
 __global__ void __launch_bounds__(EpiShape<BN>::threads, 1)
     tc_fwd_shift_kernel(const __grid_constant__ ShiftParams prm) {
     constexpr int EPI_WARPS = EpiShape<BN>::warps;
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(EpiShape<BN>::threads, 1)
                 }
                 const int col0 = nt * prm.bn + j * 32;
                 if (!rows_ok || col0 >= prm.epi.K) continue;
-                epilogue_chunk<FP8, EpiShape<BN>::nbuf>(v, prm.epi, &prm.tmY, xs, col0, q0, n * prm.P + p, lane, sbuf,
+                epilogue_chunk<FP8, EpiShape<BN>::nbuf, FUSED>(v, prm.epi, &prm.tmY, xs, col0, q0, n * prm.P + p, lane, sbuf,
                                     ebuf);
             }
             if (!released) {
@@ -428,17 +429,23 @@ size_t smem_bytes(const Dims &d, int bn, const Plan &p) {
            EPI_TOTAL + BAR_BYTES;
 }
 
-template <int BN, bool FP8>
-gbconv_status_t launch(const ShiftParams &prm, size_t smem, int grid, cudaStream_t st) {
+template <int BN, bool FP8, bool FUSED>
+gbconv_status_t launch_one(const ShiftParams &prm, size_t smem, int grid, cudaStream_t st) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(tc_fwd_shift_kernel<BN, FP8>,
+        attr_err = cudaFuncSetAttribute(tc_fwd_shift_kernel<BN, FP8, FUSED>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     });
     if (attr_err != cudaSuccess) return cuda_status(attr_err);
-    return cuda_status(
-        launch_pdl(tc_fwd_shift_kernel<BN, FP8>, dim3(grid), dim3(EpiShape<BN>::threads), smem, st, prm));
+    return cuda_status(launch_pdl(tc_fwd_shift_kernel<BN, FP8, FUSED>, dim3(grid),
+                                  dim3(EpiShape<BN>::threads), smem, st, prm));
+}
+
+template <int BN, bool FP8>
+gbconv_status_t launch(const ShiftParams &prm, size_t smem, int grid, cudaStream_t st) {
+    return (prm.epi.alpha || prm.epi.z) ? launch_one<BN, FP8, true>(prm, smem, grid, st)
+                                        : launch_one<BN, FP8, false>(prm, smem, grid, st);
 }
 
 }  // namespace
@@ -458,7 +465,8 @@ bool tc_fwd_shift_preferred(const Dims &d, int block_n) {
 
 gbconv_status_t launch_tc_fwd_shift(const Dims &d, const TcConfig &cfg, const void *x,
                                     const void *w, const float *bias, const float *x_scale,
-                                    const float *w_scale, void *y, cudaStream_t st) {
+                                    const float *w_scale, void *y, cudaStream_t st,
+                                    const Fused &fz) {
     const int bn = cfg.block_n;
     if (bn != 32 && bn != 64 && bn != 128 && bn != 256) return GBCONV_ERR_INVALID_ARG;
     Plan pl;
@@ -513,7 +521,8 @@ gbconv_status_t launch_tc_fwd_shift(const Dims &d, const TcConfig &cfg, const vo
     prm.stages_b = pl.stages_b;
     prm.raster = cfg.raster;
     prm.epi = EpiArgs{d.K, (d.flags & GBCONV_FLAG_RELU) ? 1 : 0, of32 ? 1 : 0,
-                      (d.flags & GBCONV_FLAG_BIAS) ? bias : nullptr, w_scale};
+                      (d.flags & GBCONV_FLAG_BIAS) ? bias : nullptr, w_scale, fz.alpha, fz.z,
+                      d.M(), d.Q};
     prm.x_scale = x_scale;
     prm.guard = make_guard();
     if (!prm.guard.err) return GBCONV_ERR_CUDA;

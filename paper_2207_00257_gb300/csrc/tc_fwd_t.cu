@@ -104,6 +104,8 @@ struct TParams {
     int band_bytes, band_stride, w_resident, stages_a, stages_b;
     int relu, out_f32;
     const float *bias, *x_scale, *w_scale;
+    const float *alpha;  // fused per-channel scale (folded batch norm) or null
+    const void *z;       // fused residual of y's shape and dtype (may be y) or null
     void *y;  // [N][P][Q][K], BF16 or FP32
     Guard guard;
 };
@@ -117,6 +119,7 @@ struct Tile {
     int n, p0, kt, f0, f1, P, Q, oa, ob;
 };
 
+template <bool OPH>
 __device__ __forceinline__ Tile tdecode(const TParams &p, int tile) {
     Tile t;
     int lt = tile, ptiles = p.p_tiles;
@@ -126,7 +129,7 @@ __device__ __forceinline__ Tile tdecode(const TParams &p, int tile) {
     t.Q = p.Q;
     t.oa = p.oa;
     t.ob = p.ob;
-    if (p.n_ophase) {
+    if (OPH) {
         int op = 0;
         while (op + 1 < p.n_ophase && tile >= p.op_tile0[op + 1]) ++op;
         lt = tile - p.op_tile0[op];
@@ -150,7 +153,9 @@ __device__ __forceinline__ Tile tdecode(const TParams &p, int tile) {
     return t;
 }
 
-template <int KT, bool FP8>
+// FUSED: the epilogue also applies the per-channel scale and the residual.
+// OPH: data-gradient launch, tiles grouped by output phase (n_ophase > 0).
+template <int KT, bool FP8, bool FUSED, bool OPH>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_constant__ TParams prm) {
     constexpr int KE = FP8 ? 128 : 64;
     constexpr int TCOLS = 2 * NPOS;          // two 256-column accumulators
@@ -240,7 +245,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
             int sa = 0, sb = 0;
             uint32_t pa = 0, pb = 0;
             int issued_a = 0, issued_b = 0;
-            if (prm.w_resident && !skip && prm.n_ophase) {
+            if (OPH && prm.w_resident && !skip) {
                 // data gradient: the first tile uses one phase's taps only, so
                 // the whole resident filter is issued up front
                 for (int seq = 0; seq < w_tiles; ++seq) {
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                 issued_w = w_tiles;
             }
             for (int tile = blockIdx.x; ok && tile < prm.num_tiles; tile += gridDim.x) {
-                const Tile T = tdecode(prm, tile);
+                const Tile T = tdecode<OPH>(prm, tile);
                 const int n = T.n, p0 = T.p0, kt = T.kt;
                 for (int cb = 0; ok && cb < prm.c_blocks; ++cb) {
                     for (int f = T.f0; ok && f < T.f1; ++f) {
@@ -347,6 +352,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
             idesc = (idesc & ~(0x1Fu << 24)) | ((uint32_t)(KT >> 4) << 24);  // M = KT
             int sa = 0, sb = 0;
             uint32_t pa = 0, pb = 0;
+            uint32_t wres_seen = 0;  // resident filter groups already waited for
             int local = 0;
             for (int tile = blockIdx.x; ok && tile < prm.num_tiles; tile += gridDim.x, ++local) {
                 const int acc = local & 1;
@@ -356,7 +362,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                     break;
                 }
                 ptx::tc_fence_after();
-                const Tile T = tdecode(prm, tile);
+                const Tile T = tdecode<OPH>(prm, tile);
                 const uint32_t d = tmem_base + (uint32_t)(acc * NPOS);
                 uint32_t accum = 0;
                 for (int cb = 0; ok && cb < prm.c_blocks; ++cb) {
@@ -372,13 +378,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                             uint32_t w_addr;
                             if (prm.w_resident) {
                                 const int seq = cb * prm.RS + ti;
-                                {  // this tile's group loaded (at once true after its first use)
-                                    if (!ptx::mbar_wait(&wres[seq / wper], 0, lim, abort_flag)) {
-                                        fail();
-                                        ok = false;
-                                        break;
+                                // the forward's first tile uses every group; a data-gradient
+                                // tile uses its phase's groups, first seen on any tile
+                                if (local == 0 || OPH) {
+                                    const int grp = seq / wper;
+                                    if (!((wres_seen >> grp) & 1u)) {  // first use of this group
+                                        if (!ptx::mbar_wait(&wres[grp], 0, lim, abort_flag)) {
+                                            fail();
+                                            ok = false;
+                                            break;
+                                        }
+                                        ptx::tc_fence_after();
+                                        wres_seen |= 1u << grp;
                                     }
-                                    ptx::tc_fence_after();
                                 }
                                 w_addr = ptx::smem_addr(sW + seq * W_TILE);
                             } else {
@@ -439,18 +451,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
         const int nchunks = prm.n_pos >> 5;
         int local = 0;
         for (int tile = blockIdx.x; tile < prm.num_tiles; tile += gridDim.x, ++local) {
-            const Tile T = tdecode(prm, tile);
+            const Tile T = tdecode<OPH>(prm, tile);
             const int n = T.n, p0 = T.p0, kt = T.kt;
             const int acc = local & 1;
             const uint32_t aph = (local >> 1) & 1;
             // per-channel constants, fetched before the accumulator is ready
-            float scl = 1.f, bia = 0.f;      // FP32 output: channel krow
-            float bs[NH][2], ss[NH][2];      // BF16 output: channels chb0 + 16h + 8s + lane/4
+            float scl = 1.f, bia = 0.f, alf = 1.f;  // FP32 output: channel krow
+            float bs[NH][2], ss[NH][2], as[NH][2];  // BF16 output: channels chb0 + 16h + 8s + lane/4
             if (prm.out_f32) {
                 const int k = kt * KT + krow;
                 if (k < prm.K) {
                     if (FP8) scl = xs * __ldg(prm.w_scale + k);
                     if (prm.bias) bia = __ldg(prm.bias + k);
+                    if (FUSED && prm.alpha) alf = __ldg(prm.alpha + k);
                 }
             } else {
 #pragma unroll
@@ -460,6 +473,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                         const int k = kt * KT + chb0 + 16 * h + 8 * s2 + (lane >> 2);
                         bs[h][s2] = (prm.bias && k < prm.K) ? __ldg(prm.bias + k) : 0.f;
                         ss[h][s2] = (FP8 && k < prm.K) ? xs * __ldg(prm.w_scale + k) : 1.f;
+                        as[h][s2] = (FUSED && prm.alpha && k < prm.K) ? __ldg(prm.alpha + k) : 1.f;
                     }
             }
             if (!ptx::mbar_wait(&tfull[acc], aph, lim, abort_flag)) {
@@ -528,8 +542,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                                     a0 = a0 * ss[h][s2];
                                     a1 = a1 * ss[h][s2];
                                 }
+                                if (FUSED && prm.alpha) {
+                                    a0 = a0 * as[h][s2];
+                                    a1 = a1 * as[h][s2];
+                                }
                                 a0 = a0 + bs[h][s2];
                                 a1 = a1 + bs[h][s2];
+                                if (FUSED && prm.z) {  // residual of positions e, e+1 of channel kz
+                                    const int kz = kw + 16 * h + 8 * s2 + (lane >> 2);
+                                    const int e = 8 * g + 2 * (lane & 3);
+                                    const __nv_bfloat16 *zp = static_cast<const __nv_bfloat16 *>(prm.z);
+                                    if (kz < prm.K) {
+                                        if (e < nvalid)
+                                            a0 = a0 + __bfloat162float(zp[(yrow + e * ystep) * prm.K + kz]);
+                                        if (e + 1 < nvalid)
+                                            a1 = a1 + __bfloat162float(
+                                                          zp[(yrow + (e + 1) * ystep) * prm.K + kz]);
+                                    }
+                                }
                                 if (prm.relu) {
                                     a0 = fmaxf(a0, 0.f);
                                     a1 = fmaxf(a1, 0.f);
@@ -566,9 +596,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                         for (int i = 0; i < NV; ++i) {
                             float a = __uint_as_float(v[i]);
                             if (FP8) a = a * scl;
+                            if (FUSED && prm.alpha) a = a * alf;
                             a = a + bia;
-                            if (prm.relu) a = fmaxf(a, 0.f);
-                            if (e0 + i < nvalid) yf[(yrow + (e0 + i) * ystep) * prm.K + k] = a;
+                            if (e0 + i < nvalid) {
+                                const size_t off = (yrow + (e0 + i) * ystep) * prm.K + k;
+                                if (FUSED && prm.z) a = a + static_cast<const float *>(prm.z)[off];
+                                if (prm.relu) a = fmaxf(a, 0.f);
+                                yf[off] = a;
+                            }
                         }
                     }
                 }
@@ -738,16 +773,24 @@ void build_taps(const Dims &d, int wx_log2, TParams *prm) {
     prm->n_phase = f_out;
 }
 
-template <int KT, bool FP8>
-gbconv_status_t launch(const TParams &prm, size_t smem, int grid, cudaStream_t st) {
+template <int KT, bool FP8, bool FUSED, bool OPH>
+gbconv_status_t launch_one(const TParams &prm, size_t smem, int grid, cudaStream_t st) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(tc_fwd_t_kernel<KT, FP8>,
+        attr_err = cudaFuncSetAttribute(tc_fwd_t_kernel<KT, FP8, FUSED, OPH>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     });
     if (attr_err != cudaSuccess) return cuda_status(attr_err);
-    return cuda_status(launch_pdl(tc_fwd_t_kernel<KT, FP8>, dim3(grid), dim3(NTHREADS), smem, st, prm));
+    return cuda_status(
+        launch_pdl(tc_fwd_t_kernel<KT, FP8, FUSED, OPH>, dim3(grid), dim3(NTHREADS), smem, st, prm));
+}
+
+// forward launches (with or without the fused epilogue)
+template <int KT, bool FP8>
+gbconv_status_t launch(const TParams &prm, size_t smem, int grid, cudaStream_t st) {
+    return (prm.alpha || prm.z) ? launch_one<KT, FP8, true, false>(prm, smem, grid, st)
+                                : launch_one<KT, FP8, false, false>(prm, smem, grid, st);
 }
 
 }  // namespace
@@ -763,7 +806,7 @@ int tc_fwd_t_tile(const Dims &d) {
 
 gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, const float *bias,
                                 const float *x_scale, const float *w_scale, void *y,
-                                cudaStream_t st) {
+                                cudaStream_t st, const Fused &fz) {
     const int kt = tc_fwd_t_tile(d);
     if (!kt) return GBCONV_ERR_UNSUPPORTED;
     TPlan pl;
@@ -829,6 +872,8 @@ gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, con
     prm.bias = (d.flags & GBCONV_FLAG_BIAS) ? bias : nullptr;
     prm.x_scale = x_scale;
     prm.w_scale = w_scale;
+    prm.alpha = fz.alpha;
+    prm.z = fz.z;
     prm.guard = make_guard();
     if (!prm.guard.err) return GBCONV_ERR_CUDA;
     const int w_slots = pl.w_resident ? d.R * d.S * pl.c_blocks : pl.stages_b;
@@ -1059,7 +1104,8 @@ gbconv_status_t launch_tc_dgrad_t(const Dims &d, const void *dy, const void *wT,
                         (size_t)w_slots * kt * 128 +
                         (kt == 128 ? epi_total<128>() : epi_total<64>()) + BAR_BYTES;
     const int grid = std::min(prm.num_tiles, sm_count());
-    return kt == 64 ? launch<64, false>(prm, smem, grid, st) : launch<128, false>(prm, smem, grid, st);
+    return kt == 64 ? launch_one<64, false, false, true>(prm, smem, grid, st)
+                    : launch_one<128, false, false, true>(prm, smem, grid, st);
 }
 
 }  // namespace gbc

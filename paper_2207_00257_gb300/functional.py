@@ -67,6 +67,36 @@ def conv2d(x, w, bias=None, stride=1, padding=0, dilation=1, relu=False, layout=
     return out
 
 
+def conv2d_fused(x, w, bias=None, scale=None, residual=None, stride=1, padding=0, dilation=1,
+                 relu=False, layout="NHWC", out_dtype=None, x_scale=None, w_scale=None, out=None):
+    """y = act(scale[k] * conv(x, w) + bias[k] + residual) through
+    conv2d_fwd_fused (batch normalisation folded into scale/bias with
+    bn_fold; residual of y's shape and dtype, may be ``out`` itself)."""
+    _check_dev(x, w, bias, scale, residual, x_scale, w_scale)
+    prob = make_problem(x, w, stride, padding, dilation, layout, out_dtype, bias is not None, relu)
+    if out is None:
+        out = torch.empty(out_shape(prob, layout), dtype=_TORCH[prob.out_dtype], device=x.device)
+    ptr = lambda t: t.data_ptr() if t is not None else 0
+    s = B.conv2d_fwd_fused(prob, x.data_ptr(), w.data_ptr(), ptr(bias), ptr(scale), ptr(residual),
+                           ptr(x_scale), ptr(w_scale), out.data_ptr(), 0, 0, _stream())
+    B.check(s, "conv2d_fwd_fused")
+    return out
+
+
+def bn_fold(gamma, bn_beta, mean, var, eps, bias=None):
+    """Folds inference batch normalisation (after a convolution with ``bias``)
+    into the fused forward's per-channel (scale, shift), on the device."""
+    _check_dev(gamma, bn_beta, mean, var, bias)
+    K = gamma.numel()
+    scale = torch.empty(K, dtype=torch.float32, device=gamma.device)
+    shift = torch.empty(K, dtype=torch.float32, device=gamma.device)
+    s = B.gbconv_bn_fold(K, gamma.data_ptr(), bn_beta.data_ptr(), mean.data_ptr(), var.data_ptr(),
+                         eps, bias.data_ptr() if bias is not None else 0, scale.data_ptr(),
+                         shift.data_ptr(), _stream())
+    B.check(s, "gbconv_bn_fold")
+    return scale, shift
+
+
 def workspace(op, prob, device):
     s, nbytes = B.gbconv_workspace_size(op, prob)
     B.check(s, "gbconv_workspace_size")
