@@ -84,7 +84,7 @@ def _load():
 class Conv:
     """Problem description: per-axis stride (u, v), padding and dilation."""
 
-    def __init__(self, N, C, H, W, K, R, S, stride=1, pad=0, dil=1, layout="NCHW"):
+    def __init__(self, N, C, H, W, K, R, S, stride=1, pad=0, dil=1, layout="NCHW", groups=1):
         su, sv = (stride, stride) if np.isscalar(stride) else stride
         ph, pw = (pad, pad) if np.isscalar(pad) else pad
         dh, dw = (dil, dil) if np.isscalar(dil) else dil
@@ -93,8 +93,9 @@ class Conv:
         self.N, self.C, self.H, self.W, self.K, self.R, self.S = N, C, H, W, K, R, S
         self.u, self.v, self.ph, self.pw, self.dh, self.dw = su, sv, ph, pw, dh, dw
         self.layout = layout
+        self.G = groups
         self.d = np.array([N, C, H, W, K, R, S, su, sv, ph, pw, dh, dw,
-                           0 if layout == "NCHW" else 1], dtype=np.int64)
+                           0 if layout == "NCHW" else 1, groups], dtype=np.int64)
         P, Q = ctypes.c_int64(), ctypes.c_int64()
         if _load().oracle_output_dims(_ptr(self.d, _i64p), ctypes.byref(P), ctypes.byref(Q)):
             raise ValueError("invalid convolution dimensions")
@@ -107,9 +108,10 @@ class Conv:
                 else (self.N, self.H, self.W, self.C))
 
     @property
-    def w_shape(self):
-        return ((self.K, self.C, self.R, self.S) if self.layout == "NCHW"
-                else (self.K, self.R, self.S, self.C))
+    def w_shape(self):  # C/G channels per output channel
+        cg = self.C // self.G
+        return ((self.K, cg, self.R, self.S) if self.layout == "NCHW"
+                else (self.K, self.R, self.S, cg))
 
     @property
     def y_shape(self):
@@ -118,7 +120,7 @@ class Conv:
 
     @property
     def flops(self):
-        return 2 * self.N * self.K * self.P * self.Q * self.C * self.R * self.S
+        return 2 * self.N * self.K * self.P * self.Q * (self.C // self.G) * self.R * self.S
 
 
 def _ptr(a, typ):

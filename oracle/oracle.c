@@ -50,7 +50,16 @@
  * S.1111.111 is NaN, largest finite 448) round-to-nearest-even with
  * saturation to +-448. Both are written from those format definitions.
  *
- * Dims are passed as int64 d[14] = {N,C,H,W,K,R,S,u,v,ph,pw,dh,dw,layout}.
+ * Channel groups (G = groups; G = C = K is the depthwise convolution): the
+ * C input and K output channels split into G equal groups, output channel k
+ * of group g = k / (K/G) reads only input channels g*(C/G) .. g*(C/G)+C/G-1,
+ * and the filter holds C/G channels per output channel:
+ *
+ *   y[n,k,p,q] = b[k] + sum_{c<C/G, r, s} x[n, g*(C/G) + c, ...] * w[k,c,r,s]
+ *
+ * (the data and weight gradients restrict their sums the same way).
+ *
+ * Dims are passed as int64 d[15] = {N,C,H,W,K,R,S,u,v,ph,pw,dh,dw,layout,G}.
  */
 #include <math.h>
 #include <pthread.h>
@@ -61,16 +70,20 @@
 
 typedef struct {
     int64_t N, C, H, W, K, R, S, u, v, ph, pw, dh, dw, layout, P, Q;
+    int64_t G, Cg, Kg;  /* groups, input and output channels per group */
 } dims_t;
 
 static int load_dims(const int64_t *d, dims_t *o) {
     o->N = d[0]; o->C = d[1]; o->H = d[2]; o->W = d[3]; o->K = d[4];
     o->R = d[5]; o->S = d[6]; o->u = d[7]; o->v = d[8]; o->ph = d[9];
-    o->pw = d[10]; o->dh = d[11]; o->dw = d[12]; o->layout = d[13];
+    o->pw = d[10]; o->dh = d[11]; o->dw = d[12]; o->layout = d[13]; o->G = d[14];
     if (o->N < 0 || o->C < 1 || o->H < 1 || o->W < 1 || o->K < 1 || o->R < 1 ||
         o->S < 1 || o->u < 1 || o->v < 1 || o->ph < 0 || o->pw < 0 ||
-        o->dh < 1 || o->dw < 1 || (o->layout != 0 && o->layout != 1))
+        o->dh < 1 || o->dw < 1 || (o->layout != 0 && o->layout != 1) || o->G < 1 ||
+        o->C % o->G != 0 || o->K % o->G != 0)
         return -1;
+    o->Cg = o->C / o->G;
+    o->Kg = o->K / o->G;
     int64_t pn = o->H + 2 * o->ph - o->dh * (o->R - 1) - 1;
     int64_t qn = o->W + 2 * o->pw - o->dw * (o->S - 1) - 1;
     if (pn < 0 || qn < 0) return -1;
@@ -91,9 +104,10 @@ static inline int64_t xi(const dims_t *D, int64_t n, int64_t c, int64_t h, int64
     return D->layout == 0 ? ((n * D->C + c) * D->H + h) * D->W + w
                           : ((n * D->H + h) * D->W + w) * D->C + c;
 }
+/* filter element (k, c, r, s), c < C/G the channel within k's group */
 static inline int64_t wi(const dims_t *D, int64_t k, int64_t c, int64_t r, int64_t s) {
-    return D->layout == 0 ? ((k * D->C + c) * D->R + r) * D->S + s
-                          : ((k * D->R + r) * D->S + s) * D->C + c;
+    return D->layout == 0 ? ((k * D->Cg + c) * D->R + r) * D->S + s
+                          : ((k * D->R + r) * D->S + s) * D->Cg + c;
 }
 static inline int64_t yi(const dims_t *D, int64_t n, int64_t k, int64_t p, int64_t q) {
     return D->layout == 0 ? ((n * D->K + k) * D->P + p) * D->Q + q
@@ -116,9 +130,9 @@ static void x_coords(const dims_t *D, int64_t i, int64_t *n, int64_t *c, int64_t
 }
 static void w_coords(const dims_t *D, int64_t i, int64_t *k, int64_t *c, int64_t *r, int64_t *s) {
     if (D->layout == 0) {
-        *s = i % D->S; i /= D->S; *r = i % D->R; i /= D->R; *c = i % D->C; *k = i / D->C;
+        *s = i % D->S; i /= D->S; *r = i % D->R; i /= D->R; *c = i % D->Cg; *k = i / D->Cg;
     } else {
-        *c = i % D->C; i /= D->C; *s = i % D->S; i /= D->S; *r = i % D->R; *k = i / D->R;
+        *c = i % D->Cg; i /= D->Cg; *s = i % D->S; i /= D->S; *r = i % D->R; *k = i / D->R;
     }
 }
 
@@ -129,13 +143,14 @@ static void w_coords(const dims_t *D, int64_t i, int64_t *k, int64_t *c, int64_t
 static void fwd_one(const dims_t *D, const double *x, const double *w, int64_t n,
                     int64_t k, int64_t p, int64_t q, double *sum, double *abssum) {
     double acc = 0.0, aacc = 0.0;
-    for (int64_t c = 0; c < D->C; ++c)
+    const int64_t c0 = (k / D->Kg) * D->Cg;  /* first input channel of k's group */
+    for (int64_t c = 0; c < D->Cg; ++c)
         for (int64_t r = 0; r < D->R; ++r)
             for (int64_t s = 0; s < D->S; ++s) {
                 int64_t h = p * D->u + r * D->dh - D->ph;
                 int64_t ww = q * D->v + s * D->dw - D->pw;
                 if (h < 0 || h >= D->H || ww < 0 || ww >= D->W) continue;
-                double a = x[xi(D, n, c, h, ww)], f = w[wi(D, k, c, r, s)];
+                double a = x[xi(D, n, c0 + c, h, ww)], f = w[wi(D, k, c, r, s)];
                 acc += a * f;
                 aacc += fabs(a) * fabs(f);
             }
@@ -147,7 +162,8 @@ static void fwd_one(const dims_t *D, const double *x, const double *w, int64_t n
 static void dgrad_one(const dims_t *D, const double *g, const double *w, int64_t n,
                       int64_t c, int64_t h, int64_t ww, double *sum, double *abssum) {
     double acc = 0.0, aacc = 0.0;
-    for (int64_t k = 0; k < D->K; ++k)
+    const int64_t grp = c / D->Cg, cl = c - grp * D->Cg;  /* c's group, channel within it */
+    for (int64_t k = grp * D->Kg; k < (grp + 1) * D->Kg; ++k)
         for (int64_t r = 0; r < D->R; ++r)
             for (int64_t s = 0; s < D->S; ++s) {
                 int64_t pn = h + D->ph - r * D->dh;   /* = p*u */
@@ -155,7 +171,7 @@ static void dgrad_one(const dims_t *D, const double *g, const double *w, int64_t
                 if (pn < 0 || qn < 0 || pn % D->u != 0 || qn % D->v != 0) continue;
                 int64_t p = pn / D->u, q = qn / D->v;
                 if (p >= D->P || q >= D->Q) continue;
-                double a = g[yi(D, n, k, p, q)], f = w[wi(D, k, c, r, s)];
+                double a = g[yi(D, n, k, p, q)], f = w[wi(D, k, cl, r, s)];
                 acc += a * f;
                 aacc += fabs(a) * fabs(f);
             }
@@ -163,17 +179,19 @@ static void dgrad_one(const dims_t *D, const double *g, const double *w, int64_t
     *abssum = aacc;
 }
 
-/* dw[k,c,r,s] = sum over n,p,q of g * x at the tap's input position. */
+/* dw[k,c,r,s] = sum over n,p,q of g * x at the tap's input position (input
+ * channel c of k's group). */
 static void wgrad_one(const dims_t *D, const double *x, const double *g, int64_t k,
                       int64_t c, int64_t r, int64_t s, double *sum, double *abssum) {
     double acc = 0.0, aacc = 0.0;
+    const int64_t cx = (k / D->Kg) * D->Cg + c;
     for (int64_t n = 0; n < D->N; ++n)
         for (int64_t p = 0; p < D->P; ++p)
             for (int64_t q = 0; q < D->Q; ++q) {
                 int64_t h = p * D->u + r * D->dh - D->ph;
                 int64_t ww = q * D->v + s * D->dw - D->pw;
                 if (h < 0 || h >= D->H || ww < 0 || ww >= D->W) continue;
-                double a = g[yi(D, n, k, p, q)], f = x[xi(D, n, c, h, ww)];
+                double a = g[yi(D, n, k, p, q)], f = x[xi(D, n, cx, h, ww)];
                 acc += a * f;
                 aacc += fabs(a) * fabs(f);
             }
@@ -264,7 +282,7 @@ static int run(job_t proto, int nthreads) {
 
 static int64_t y_count(const dims_t *D) { return D->N * D->K * D->P * D->Q; }
 static int64_t x_count(const dims_t *D) { return D->N * D->C * D->H * D->W; }
-static int64_t w_count(const dims_t *D) { return D->K * D->C * D->R * D->S; }
+static int64_t w_count(const dims_t *D) { return D->K * D->Cg * D->R * D->S; }
 
 /* ---- exported entry points ---- */
 

@@ -447,3 +447,72 @@ def test_bn_fold_definition():
         assert np.max(np.abs(alpha * v + beta - unfolded)) < 1e-12
     a0, b0 = oracle.bn_fold(gamma, bn_beta, mean, var, eps)
     assert np.allclose(b0, bn_beta - mean * a0, rtol=0, atol=1e-15)
+
+
+# ---- channel groups (G = C = K: depthwise) ----
+
+GROUP_CASES = [
+    # N, C, H, W, K, R, S, stride, pad, dil, G
+    (2, 4, 7, 6, 6, 3, 3, (1, 1), (1, 1), (1, 1), 2),
+    (1, 8, 9, 9, 8, 3, 3, (2, 2), (1, 1), (1, 1), 8),     # depthwise
+    (2, 6, 8, 7, 12, 3, 2, (1, 2), (1, 0), (2, 1), 6),    # depthwise, multiplier 2
+    (1, 12, 9, 8, 8, 5, 5, (1, 1), (2, 2), (1, 1), 4),
+    (2, 16, 6, 6, 16, 1, 1, (1, 1), (0, 0), (1, 1), 16),  # 1x1 depthwise: a per-channel scale
+]
+
+
+@pytest.mark.parametrize("case", GROUP_CASES)
+@pytest.mark.parametrize("layout", ["NCHW", "NHWC"])
+def test_groups_match_torch_library(case, layout):
+    """Forward, data and weight gradients with channel groups against PyTorch's
+    float64 conv2d(groups=G) and its autograd."""
+    N, C, H, W, K, R, S, st, pd, dl, G = case
+    p = Conv(N, C, H, W, K, R, S, st, pd, dl, layout, groups=G)
+    r = _rng(21)
+    x = torch.from_numpy(r.normal(size=(N, C, H, W))).requires_grad_()
+    w = torch.from_numpy(r.normal(size=(K, C // G, R, S))).requires_grad_()
+    b = torch.from_numpy(r.normal(size=K))
+    y = torch.nn.functional.conv2d(x, w, b, stride=st, padding=pd, dilation=dl, groups=G)
+    g = torch.from_numpy(r.normal(size=tuple(y.shape)))
+    (y * g).sum().backward()
+    yo = oracle.conv2d_fwd(p, _to_layout(x.detach().numpy(), layout),
+                           _to_layout(w.detach().numpy(), layout), b.numpy())
+    assert np.max(np.abs(_from_layout(yo, layout) - y.detach().numpy())) < 1e-11
+    go = _to_layout(g.numpy(), layout)
+    dx = oracle.conv2d_dgrad(p, go, _to_layout(w.detach().numpy(), layout))
+    dw = oracle.conv2d_wgrad(p, _to_layout(x.detach().numpy(), layout), go)
+    assert np.max(np.abs(_from_layout(dx, layout) - x.grad.numpy())) < 1e-11
+    assert np.max(np.abs(_from_layout(dw, layout) - w.grad.numpy())) < 1e-10
+
+
+@pytest.mark.parametrize("case", GROUP_CASES[:4])
+def test_groups_are_independent_convolutions(case):
+    """Output channels of group g equal an ungrouped convolution of x's channel
+    slice g with the filters of group g (exact: the same sum in the same order)."""
+    N, C, H, W, K, R, S, st, pd, dl, G = case
+    p = Conv(N, C, H, W, K, R, S, st, pd, dl, "NCHW", groups=G)
+    r = _rng(22)
+    x, w, b = r.normal(size=(N, C, H, W)), r.normal(size=(K, C // G, R, S)), r.normal(size=K)
+    y = oracle.conv2d_fwd(p, x, w, b)
+    cg, kg = C // G, K // G
+    for g in range(G):
+        pg = Conv(N, cg, H, W, kg, R, S, st, pd, dl, "NCHW")
+        yg = oracle.conv2d_fwd(pg, np.ascontiguousarray(x[:, g * cg:(g + 1) * cg]),
+                               np.ascontiguousarray(w[g * kg:(g + 1) * kg]), b[g * kg:(g + 1) * kg])
+        assert np.array_equal(y[:, g * kg:(g + 1) * kg], yg)
+
+
+def test_groups_adjoint_identities():
+    N, C, H, W, K, R, S, st, pd, dl, G = GROUP_CASES[2]
+    p = Conv(N, C, H, W, K, R, S, st, pd, dl, "NHWC", groups=G)
+    r = _rng(23)
+    x, w = r.normal(size=p.x_shape), r.normal(size=p.w_shape)
+    g = r.normal(size=p.y_shape)
+    lhs = np.sum(oracle.conv2d_fwd(p, x, w) * g)
+    assert abs(lhs - np.sum(x * oracle.conv2d_dgrad(p, g, w))) < 1e-9 * max(1, abs(lhs))
+    assert abs(lhs - np.sum(w * oracle.conv2d_wgrad(p, x, g))) < 1e-9 * max(1, abs(lhs))
+
+
+def test_groups_must_divide_channels():
+    with pytest.raises(ValueError):
+        Conv(1, 6, 5, 5, 4, 3, 3, groups=4)
