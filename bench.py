@@ -286,7 +286,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline BF16 layer set (skip FP32/FP8/grouped/backward)")
-    ap.add_argument("--sections", default="fp32,fp8,grouped,backward",
+    ap.add_argument("--sections", default="fp32,fp8,grouped,backward,fused,groups",
                     help="comma list of extra workloads to run after the headline layer set")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     args = ap.parse_args()
@@ -367,9 +367,13 @@ def run_ours(args, rank, world, local):
     if not args.no_extras:
         sections = [x for x in args.sections.split(",") if x]
         fns = {"fp32": bench_fp32, "fp8": bench_fp8, "grouped": bench_grouped,
-               "backward": bench_backward}
+               "backward": bench_backward, "fused": bench_fused, "groups": bench_groups}
         for name in sections:
-            out[name] = fns[name](torch, dev, args, dist_on, pk)
+            try:
+                out[name] = fns[name](torch, dev, args, dist_on, pk)
+            except Exception as e:  # an extra workload never takes the headline line down
+                torch.cuda.synchronize()
+                out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
     sampler.stop()
     out["clocks"] = sampler.summary(*clocks_window)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -598,6 +602,102 @@ def bench_backward(torch, dev, args, dist_on, pk):
                               "subpixel_tc_tflops": round(f2 / (res["launch_us"][2] * 1e-6) / 1e12, 1),
                               "cuda_core_us": round(res["launch_us"][3], 1),
                               "cuda_core_tflops": round(f2 / (res["launch_us"][3] * 1e-6) / 1e12, 2)}}
+
+
+def bench_fused(torch, dev, args, dist_on, pk):
+    """End of a ResNet-50 bottleneck block (1x1 64 -> 256 at 56x56, batch 32):
+    convolution, inference batch norm, identity-shortcut add and ReLU. Fused:
+    one conv2d_fwd_fused launch with the folded (scale, shift) and the
+    shortcut as residual. Unfused: the plain forward followed by the same
+    epilogue as PyTorch elementwise operations (reference point only)."""
+    from paper_2207_00257_gb300 import binding as B
+    from paper_2207_00257_gb300 import functional as F
+    from paper_2207_00257_gb300.synth import make_inputs, resnet_layers
+    sh = resnet_layers(32)[2]
+    x, w, b, _ = make_inputs(sh, 7)
+    g = torch.Generator().manual_seed(8)
+    xb, wb = x.bfloat16().to(dev), w.bfloat16().to(dev)
+    gamma = (torch.rand(sh.K, generator=g) + 0.5).to(dev)
+    beta, mean = torch.randn(sh.K, generator=g).to(dev), (0.1 * torch.randn(sh.K, generator=g)).to(dev)
+    var = (torch.rand(sh.K, generator=g) + 0.5).to(dev)
+    scale, shift = F.bn_fold(gamma, beta, mean, var, 1e-5, bias=b.to(dev))
+    z = torch.randn(sh.y_shape(), generator=g).bfloat16().to(dev)
+    y = torch.empty(sh.y_shape(), dtype=torch.bfloat16, device=dev)
+    y2 = torch.empty_like(y)
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                     B.GBCONV_BF16, B.GBCONV_BF16, B.GBCONV_NHWC, B.GBCONV_FLAG_BIAS |
+                     B.GBCONV_FLAG_RELU)
+    prob0 = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                      B.GBCONV_BF16, B.GBCONV_BF16, B.GBCONV_NHWC, 0)
+    sc4 = scale.view(1, 1, 1, -1)
+    sh4 = shift.view(1, 1, 1, -1)
+
+    def fused(i, stream):
+        B.check(B.conv2d_fwd_fused(prob, xb.data_ptr(), wb.data_ptr(), shift.data_ptr(),
+                                   scale.data_ptr(), z.data_ptr(), 0, 0, y.data_ptr(), 0, 0,
+                                   stream), "fused")
+
+    def unfused(i, stream):
+        B.check(B.conv2d_fwd(prob0, xb.data_ptr(), wb.data_ptr(), 0, 0, 0, y2.data_ptr(), 0, 0,
+                             stream), "conv")
+        s = torch.cuda.ExternalStream(stream)
+        with torch.cuda.stream(s):
+            torch.relu_(y2.float().mul_(sc4).add_(sh4).add_(z.float())).to(torch.bfloat16)
+
+    class L:
+        def __init__(s, f):
+            s.launch = f
+
+    steps = max(3, min(args.steps, 20))
+    res = bench_layers([L(fused), L(unfused)], steps, 3, 1, torch, dist_on)
+    f = sh.flops
+    return {"workload": "bottleneck_end_" + sh.tag + "_bn_residual_relu",
+            "fused_us": round(res["launch_us"][0], 1),
+            "fused_tflops": round(f / (res["launch_us"][0] * 1e-6) / 1e12, 1),
+            "unfused_conv_plus_torch_elementwise_us": round(res["launch_us"][1], 1),
+            "bytes_fused_MB": round((xb.numel() + wb.numel() + z.numel() + y.numel()) * 2 / 1e6, 1)}
+
+
+def bench_groups(torch, dev, args, dist_on, pk):
+    """Channel-grouped layers, batch 32, BF16 NHWC: a depthwise 3x3 (G = C = K
+    = 128 at 56x56, memory-bound: reported against HBM), a ResNeXt-style 3x3
+    with 32 groups of 4 channels (C = K = 128 at 56x56, CUDA cores), and a
+    two-group 3x3 (C = K = 256 at 28x28, tensor cores per group)."""
+    from paper_2207_00257_gb300 import binding as B
+    cases = [("depthwise_3x3_128ch_56", 128, 56, 128, 128),
+             ("resnext_3x3_32x4ch_56", 128, 56, 128, 32),
+             ("two_groups_3x3_256ch_28", 256, 28, 256, 2)]
+    layers, meta = [], []
+    g = torch.Generator().manual_seed(9)
+    for tag, C, HW, K, G in cases:
+        x = torch.randn(32, HW, HW, C, generator=g).bfloat16().to(dev)
+        w = (torch.randn(K, 3, 3, C // G, generator=g) / (3 * (C // G) ** 0.5)).bfloat16().to(dev)
+        b = (torch.rand(K, generator=g) * 0.2 - 0.1).to(dev)
+        y = torch.empty(32, HW, HW, K, dtype=torch.bfloat16, device=dev)
+        prob = B.problem(32, C, HW, HW, K, 3, 3, 1, 1, 1, B.GBCONV_BF16, B.GBCONV_BF16,
+                         B.GBCONV_NHWC, B.GBCONV_FLAG_BIAS | B.GBCONV_FLAG_RELU, G)
+
+        def launch(i, stream, prob=prob, x=x, w=w, b=b, y=y):
+            B.check(B.conv2d_fwd(prob, x.data_ptr(), w.data_ptr(), b.data_ptr(), 0, 0,
+                                 y.data_ptr(), 0, 0, stream), "grouped-channel conv")
+
+        class L:
+            pass
+        lay = L()
+        lay.launch = launch
+        layers.append(lay)
+        flops = 2 * 32 * K * HW * HW * (C // G) * 9
+        nbytes = (x.numel() + y.numel()) * 2 + w.numel() * 2 + K * 4
+        meta.append((tag, G, flops, nbytes))
+    steps = max(3, min(args.steps, 20))
+    res = bench_layers(layers, steps, 3, 1, torch, dist_on)
+    out = []
+    for (tag, G, flops, nbytes), us in zip(meta, res["launch_us"]):
+        out.append({"workload": tag, "groups": G, "us": round(us, 1),
+                    "tflops": round(flops / (us * 1e-6) / 1e12, 2),
+                    "gbs": round(nbytes / (us * 1e-6) / 1e9, 1),
+                    "frac_of_hbm": round(nbytes / (us * 1e-6) / 1e9 / pk["hbm_gbs"], 3)})
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -72,7 +72,18 @@ typedef enum { GBCONV_OP_FWD = 0, GBCONV_OP_DGRAD = 1, GBCONV_OP_WGRAD = 2 } gbc
  *                 y = b + x_scale * w_scale[k] * sum(xq * wq))
  * Padding must be in [0, 127] and dilation*(R-1) <= 127 (the im2col TMA range).
  * N may be 0 (an empty batch): conv2d_fwd and conv2d_dgrad then do nothing
- * (tensor pointers may be NULL) and conv2d_wgrad writes zeros to dw and db. */
+ * (tensor pointers may be NULL) and conv2d_wgrad writes zeros to dw and db.
+ *
+ * Channel groups (groups = G > 1; G = C = K is the depthwise convolution):
+ * C and K must be multiples of G; output channel k of group g = k / (K/G)
+ * reads input channels g*C/G .. g*C/G + C/G - 1, and w holds C/G channels
+ * per output channel: [K,R,S,C/G] (NHWC) or [K,C/G,R,S] (NCHW). The forward
+ * (conv2d_fwd, conv2d_fwd_fused) supports groups: BF16/E4M3 NHWC with C/G
+ * and K/G multiples of 8 (16 for E4M3) runs each group on the tensor cores
+ * in one persistent launch; depthwise NHWC (C/G = K/G = 1, C % 8 == 0) runs a
+ * CUDA-core kernel with 16-byte channel vectors; the rest (F32/BF16 in) runs
+ * the CUDA-core implicit GEMM per group. conv2d_dgrad, conv2d_wgrad and
+ * conv2d_grouped return GBCONV_ERR_UNSUPPORTED for G > 1. */
 typedef struct {
     int32_t N, C, H, W, K, R, S;
     int32_t stride_h, stride_w;
@@ -82,6 +93,7 @@ typedef struct {
     int32_t out_dtype;  /* gbconv_dtype_t */
     int32_t layout;     /* gbconv_layout_t */
     uint32_t flags;     /* GBCONV_FLAG_* */
+    int32_t groups;     /* channel groups G (0 or 1: none); see below */
 } gbconv_problem_t;
 
 /* Launch configuration of one convolution (chosen by the autotuner or set by

@@ -41,7 +41,8 @@ EXPORTS = [
 class gbconv_problem_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
                 ("N", "C", "H", "W", "K", "R", "S", "stride_h", "stride_w", "pad_h", "pad_w",
-                 "dil_h", "dil_w", "in_dtype", "out_dtype", "layout")] + [("flags", ctypes.c_uint32)]
+                 "dil_h", "dil_w", "in_dtype", "out_dtype", "layout")] + [("flags", ctypes.c_uint32),
+                                                                          ("groups", ctypes.c_int32)]
 
 
 class gbconv_config_t(ctypes.Structure):
@@ -131,12 +132,12 @@ def _vp(v):
 
 
 def problem(N, C, H, W, K, R, S, stride=(1, 1), pad=(0, 0), dil=(1, 1), in_dtype=GBCONV_BF16,
-            out_dtype=GBCONV_BF16, layout=GBCONV_NHWC, flags=0) -> gbconv_problem_t:
+            out_dtype=GBCONV_BF16, layout=GBCONV_NHWC, flags=0, groups=1) -> gbconv_problem_t:
     st = (stride, stride) if isinstance(stride, int) else tuple(stride)
     pd = (pad, pad) if isinstance(pad, int) else tuple(pad)
     dl = (dil, dil) if isinstance(dil, int) else tuple(dil)
     return gbconv_problem_t(N, C, H, W, K, R, S, st[0], st[1], pd[0], pd[1], dl[0], dl[1],
-                            in_dtype, out_dtype, layout, flags)
+                            in_dtype, out_dtype, layout, flags, groups)
 
 
 # ---- the entry points, C names, C argument order ----

@@ -64,9 +64,10 @@ std::map<std::string, TcConfig> g_tune;
 std::string problem_key(int op, const gbconv_problem_t &p) {
     DevInfo *di = dev_info();
     char buf[512];
-    snprintf(buf, sizeof buf, "%d|%d,%d,%d,%d,%d,%d,%d|%d,%d,%d,%d,%d,%d|%d,%d,%d,%u|%s", op, p.N,
-             p.C, p.H, p.W, p.K, p.R, p.S, p.stride_h, p.stride_w, p.pad_h, p.pad_w, p.dil_h,
-             p.dil_w, p.in_dtype, p.out_dtype, p.layout, p.flags, di ? di->name.c_str() : "?");
+    snprintf(buf, sizeof buf, "%d|%d,%d,%d,%d,%d,%d,%d|%d,%d,%d,%d,%d,%d|%d,%d,%d,%u|g%d|%s", op,
+             p.N, p.C, p.H, p.W, p.K, p.R, p.S, p.stride_h, p.stride_w, p.pad_h, p.pad_w, p.dil_h,
+             p.dil_w, p.in_dtype, p.out_dtype, p.layout, p.flags, p.groups > 1 ? p.groups : 1,
+             di ? di->name.c_str() : "?");
     return buf;
 }
 
@@ -91,6 +92,8 @@ gbconv_status_t make_dims(const gbconv_problem_t *p, Dims *d) {
         p->out_dtype > GBCONV_E4M3 || (p->layout != GBCONV_NCHW && p->layout != GBCONV_NHWC))
         return GBCONV_ERR_INVALID_ARG;
     if (p->flags & ~(GBCONV_FLAG_BIAS | GBCONV_FLAG_RELU)) return GBCONV_ERR_INVALID_ARG;
+    const int G = p->groups > 1 ? p->groups : 1;
+    if (p->groups < 0 || p->C % G != 0 || p->K % G != 0) return GBCONV_ERR_INVALID_ARG;
     long long pn = (long long)p->H + 2ll * p->pad_h - (long long)p->dil_h * (p->R - 1) - 1;
     long long qn = (long long)p->W + 2ll * p->pad_w - (long long)p->dil_w * (p->S - 1) - 1;
     if (pn < 0 || qn < 0) return GBCONV_ERR_INVALID_ARG;
@@ -113,6 +116,7 @@ gbconv_status_t make_dims(const gbconv_problem_t *p, Dims *d) {
     d->in_dtype = p->in_dtype;
     d->out_dtype = p->out_dtype;
     d->flags = p->flags;
+    d->G = G;
     // element counts must fit the kernels' 64-bit offsets comfortably
     const long long lim = 1ll << 40;
     if ((long long)d->N * d->C * d->H * d->W >= lim || (long long)d->N * d->K * d->P * d->Q >= lim ||
@@ -197,10 +201,52 @@ size_t wgrad_ws_bytes(const Dims &d, int slices) {
     return round256(((size_t)slices * kcrs + (size_t)BIAS_SLICES * d.K) * sizeof(float));
 }
 
+// Forward of a layer with channel groups (d.G > 1): depthwise kernel, one
+// persistent tensor-core launch over the groups as separate problems (BF16
+// NHWC, C/G and K/G multiples of 8, no fused scale or residual), else the
+// CUDA-core implicit GEMM per group.
+gbconv_status_t do_fwd_groups(const Dims &d, const void *x, const void *w, const float *bias,
+                              const float *x_scale, const float *w_scale, void *y,
+                              cudaStream_t st, const Fused &fz) {
+    (void)x_scale;
+    (void)w_scale;
+    if (d.in_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
+    if (d.in_dtype == GBCONV_F32 && d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
+    const int Cg = d.C / d.G, Kg = d.K / d.G;
+    if (depthwise_supported(d) && aligned16(x) && aligned16(y) && (!fz.z || aligned16(fz.z)))
+        return launch_depthwise(d, x, w, bias, y, st, fz);
+    if (d.in_dtype == GBCONV_BF16 && d.layout == GBCONV_NHWC && Cg % 8 == 0 && Kg % 8 == 0 &&
+        !fz.alpha && !fz.z && aligned16(x) && aligned16(w) && aligned16(y)) {
+        const int ebo = d.out_dtype == GBCONV_F32 ? 4 : 2;
+        std::vector<Dims> dg(d.G, d);
+        std::vector<TcConfig> cfg(d.G);
+        std::vector<const void *> xs(d.G), ws(d.G);
+        std::vector<const float *> bs(d.G);
+        std::vector<void *> ys(d.G);
+        for (int g = 0; g < d.G; ++g) {
+            Dims &e = dg[g];
+            e.C = Cg;
+            e.K = Kg;
+            e.G = 1;
+            e.ldxc = d.C;
+            e.ldyc = d.K;
+            cfg[g] = tc_fwd_default_config(e);
+            xs[g] = static_cast<const char *>(x) + (size_t)g * Cg * 2;
+            ws[g] = static_cast<const char *>(w) + (size_t)g * Kg * d.R * d.S * Cg * 2;
+            bs[g] = ((d.flags & GBCONV_FLAG_BIAS) && bias) ? bias + (size_t)g * Kg : nullptr;
+            ys[g] = static_cast<char *>(y) + (size_t)g * Kg * ebo;
+        }
+        return launch_tc_grouped(d.G, dg.data(), cfg.data(), xs.data(), ws.data(), bs.data(),
+                                 ys.data(), st);
+    }
+    return launch_simt_fwd(d, x, w, bias, y, st, fz);
+}
+
 gbconv_status_t do_fwd(const Dims &d, const TcConfig &cfg, const void *x, const void *w,
                        const float *bias, const float *x_scale, const float *w_scale, void *y,
                        cudaStream_t st, const Fused &fz = Fused{}) {
     if (d.M() == 0) return GBCONV_OK;
+    if (d.G > 1) return do_fwd_groups(d, x, w, bias, x_scale, w_scale, y, st, fz);
     if (d.in_dtype == GBCONV_F32) {
         if (d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
         return launch_simt_fwd(d, x, w, bias, y, st, fz);
@@ -313,6 +359,7 @@ gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, 
     if (!bytes) return GBCONV_ERR_INVALID_ARG;
     *bytes = 0;
     if (op == GBCONV_OP_FWD) return GBCONV_OK;
+    if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;  // grouped gradients are not implemented
     if (op == GBCONV_OP_DGRAD) {
         Dims t;
         if (dgrad_as_fwd(d, &t) || tc_dgrad_t_supported(d))
@@ -377,6 +424,7 @@ gbconv_status_t conv2d_dgrad(const gbconv_problem_t *prob, const void *dy, const
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
+    if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;
     if (d.N == 0) return GBCONV_OK;  // empty batch: dx is empty
     if (!dy || !w || !dx || dx == dy || dx == w) return GBCONV_ERR_INVALID_ARG;
     return do_dgrad(d, config_for(GBCONV_OP_DGRAD, *prob, d), dy, w, dx, ws, ws_bytes,
@@ -389,6 +437,7 @@ gbconv_status_t conv2d_wgrad(const gbconv_problem_t *prob, const void *x, const 
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
+    if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;
     if (!dw || (d.N > 0 && (!x || !dy))) return GBCONV_ERR_INVALID_ARG;
     return do_wgrad(d, config_for(GBCONV_OP_WGRAD, *prob, d), x, dy, dw, db, ws, ws_bytes,
                     static_cast<cudaStream_t>(stream));
@@ -407,6 +456,7 @@ gbconv_status_t conv2d_grouped(int32_t count, const gbconv_problem_t *probs, con
     for (int i = 0; i < count; ++i) {
         gbconv_status_t s = make_dims(&probs[i], &d[i]);
         if (s != GBCONV_OK) return s;
+        if (d[i].G > 1) return GBCONV_ERR_UNSUPPORTED;
         if (d[i].in_dtype != GBCONV_BF16 || d[i].out_dtype != GBCONV_BF16 ||
             d[i].layout != GBCONV_NHWC)
             return GBCONV_ERR_UNSUPPORTED;
@@ -475,6 +525,7 @@ gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
     if (!a || !b || !out || op < GBCONV_OP_FWD || op > GBCONV_OP_WGRAD) return GBCONV_ERR_INVALID_ARG;
+    if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;  // grouped layers have no tunable configuration
     if (reps < 1) reps = 1;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const TcConfig base = config_for(op, *prob, d);
@@ -672,6 +723,7 @@ gbconv_status_t conv2d_dgrad_noalloc(const gbconv_problem_t *prob, const void *d
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
+    if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;
     if (d.N == 0) return GBCONV_OK;
     if (!dy || !w || !dx || dx == dy || dx == w) return GBCONV_ERR_INVALID_ARG;
     if (d.in_dtype == GBCONV_E4M3 || d.out_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;

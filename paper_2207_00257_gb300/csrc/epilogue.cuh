@@ -98,6 +98,79 @@ __device__ __forceinline__ void load_residual(const EpiArgs &pa, int col0, int c
 
 // FUSED instantiations also apply the per-channel scale and the residual
 // (EpiArgs::alpha, EpiArgs::z); the others ignore both fields.
+// Asks L2 for the residual values this lane will add for a chunk at columns
+// col0 .. col0+31 (the same rows as load_residual), ahead of the accumulator.
+__device__ __forceinline__ void prefetch_residual(const EpiArgs &pa, int col0, int c1, int c2,
+                                                  int lane) {
+    long long row;
+    bool valid;
+    if (c2 < 0) {
+        row = (long long)c1 + lane;
+        valid = row < pa.M;
+    } else {
+        row = (long long)c2 * pa.Q + c1 + lane;
+        valid = c1 + lane < pa.Q;
+    }
+    if (!valid || col0 >= pa.K) return;
+    const int eb = pa.out_f32 ? 4 : 2;
+    const char *p = static_cast<const char *>(pa.z) + (row * pa.K + col0) * eb;
+    ptx::prefetch_l2(p);
+    ptx::prefetch_l2(p + 32 * eb - 1);  // the chunk's last byte (may be the next line)
+}
+
+// Fused epilogue of one BF16-output chunk whose residual tile was brought into
+// the 2 KB staging buffer `b` by a TMA load with the store's own map shape
+// (32 rows x 64 B, 64-byte swizzle): each lane reads its row's 32 residual
+// values from the buffer, adds them (after scale and bias), writes the
+// results over them in place and the buffer is stored with one TMA store.
+// The caller has waited for the load.
+template <bool FP8>
+__device__ __forceinline__ void epilogue_chunk_zsmem(const uint32_t (&v)[32], const EpiArgs &pa,
+                                                     const CUtensorMap *tmY, float xs, int col0,
+                                                     int c1, int c2, int lane, uint8_t *b) {
+    float scl = 1.f, bl = 0.f, al = 1.f;
+    const int mycol = col0 + lane;
+    if (mycol < pa.K) {
+        if (FP8) scl = xs * __ldg(pa.w_scale + mycol);
+        if (pa.bias) bl = __ldg(pa.bias + mycol);
+        if (pa.alpha) al = __ldg(pa.alpha + mycol);
+    }
+    uint8_t *row = b + lane * 64;
+    float f[32];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(row + ((c ^ ((lane >> 1) & 3)) << 4));
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 z2 = __bfloat1622float2(h[i]);
+            f[8 * c + 2 * i] = z2.x;
+            f[8 * c + 2 * i + 1] = z2.y;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        float a = __uint_as_float(v[i]);
+        if (FP8) a = a * __shfl_sync(0xffffffffu, scl, i);
+        if (pa.alpha) a = a * __shfl_sync(0xffffffffu, al, i);
+        if (pa.bias) a = a + __shfl_sync(0xffffffffu, bl, i);
+        a = a + f[i];
+        if (pa.relu) a = fmaxf(a, 0.f);
+        f[i] = a;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<uint4 *>(row + ((c ^ ((lane >> 1) & 3)) << 4)) =
+            make_uint4(pack_bf16(f[8 * c], f[8 * c + 1]), pack_bf16(f[8 * c + 2], f[8 * c + 3]),
+                       pack_bf16(f[8 * c + 4], f[8 * c + 5]), pack_bf16(f[8 * c + 6], f[8 * c + 7]));
+    ptx::fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+        store_chunk(tmY, b, col0, c1, c2);
+        ptx::bulk_commit();
+    }
+}
+
 template <bool FP8, int NBUF, bool FUSED = false>
 __device__ __forceinline__ void epilogue_chunk(const uint32_t (&v)[32], const EpiArgs &pa,
                                                const CUtensorMap *tmY, float xs, int col0,

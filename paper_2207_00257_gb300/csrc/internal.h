@@ -18,7 +18,12 @@ struct Dims {
     int layout;        // GBCONV_NCHW / GBCONV_NHWC
     int in_dtype, out_dtype;
     unsigned flags;
+    int G = 1;         // channel groups (C and K are the totals)
+    int ldxc = 0;      // NHWC channel stride of x's pixel rows when > 0 (else C): one
+    int ldyc = 0;      // group of a grouped layer run as its own problem (else K)
     long long M() const { return (long long)N * P * Q; }
+    int xstride() const { return ldxc > 0 ? ldxc : C; }
+    int ystride() const { return ldyc > 0 ? ldyc : K; }
 };
 
 // Parameters every kernel gets for its bounded waits and error report.
@@ -45,8 +50,13 @@ int sm_count();                       // SMs of the current device
 gbconv_status_t cuda_status(cudaError_t e);
 
 // simt.cu: CUDA-core FP32-accumulate kernels (any layout/stride/dilation).
+// Forward with d.G >= 1 channel groups (one grid layer per group).
 gbconv_status_t launch_simt_fwd(const Dims &d, const void *x, const void *w, const float *bias,
                                 void *y, cudaStream_t st, const Fused &fz = Fused{});
+// depthwise.cu: NHWC depthwise forward (G = C = K), 8 channels per thread.
+bool depthwise_supported(const Dims &d);
+gbconv_status_t launch_depthwise(const Dims &d, const void *x, const void *w, const float *bias,
+                                 void *y, cudaStream_t st, const Fused &fz = Fused{});
 gbconv_status_t launch_simt_dgrad(const Dims &d, const void *g, const void *w, void *dx,
                                   cudaStream_t st);
 // Partial sums of dw per slice: ws[slice][K*C*R*S] in the filter layout.

@@ -46,10 +46,12 @@ __device__ __forceinline__ void stf<__nv_bfloat16>(__nv_bfloat16 *p, float v) {
 
 struct DimsK {  // the kernel-side copy of the problem
     int N, C, H, W, K, R, S, P, Q, u, v, ph, pw, dh, dw;
+    int Cg, Kg;    // channels per group (forward with groups; else C and K)
 };
 
 __host__ DimsK to_k(const Dims &d) {
-    return DimsK{d.N, d.C, d.H, d.W, d.K, d.R, d.S, d.P, d.Q, d.u, d.v, d.ph, d.pw, d.dh, d.dw};
+    return DimsK{d.N, d.C, d.H, d.W, d.K, d.R, d.S, d.P, d.Q, d.u, d.v, d.ph, d.pw, d.dh, d.dw,
+                 d.C / d.G, d.K / d.G};
 }
 
 // ---------------------------------------------------------------------------
@@ -128,7 +130,9 @@ __global__ void __launch_bounds__(NT) simt_igemm(L ldr) {
 
 // ---------------------------------------------------------------------------
 // Forward: GEMM rows m = (n,p,q) over N*P*Q, columns = output channel k,
-// reduction over (r, s, c) with 16 channels of one tap per k-tile.
+// reduction over (r, s, c) with 16 channels of one tap per k-tile. With
+// channel groups, grid layer z = group g: columns are the group's K/G output
+// channels and the reduction runs over its C/G input channels.
 // ---------------------------------------------------------------------------
 template <typename Ti, typename To, bool NHWC>
 struct FwdLoader {
@@ -145,6 +149,7 @@ struct FwdLoader {
     const To *z;         // fused: residual of y's shape and layout (may be null)
     // per-thread state
     int m0, n0, t;
+    int cx0, k0g;  // this group's first input and output channel
     long long xb[8];
     int hb[8], wb[8];
 
@@ -152,6 +157,8 @@ struct FwdLoader {
         t = tid;
         m0 = blockIdx.x * BM;
         n0 = blockIdx.y * BN;
+        cx0 = blockIdx.z * d.Cg;
+        k0g = blockIdx.z * d.Kg;
         const long long M = (long long)d.N * d.P * d.Q;
         const int cnt = NHWC ? 8 : 1;
         for (int i = 0; i < cnt; ++i) {
@@ -182,8 +189,8 @@ struct FwdLoader {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 int h = hb[i] + r * d.dh, ww = wb[i] + s * d.dw;
-                bool ok = c < d.C && h >= 0 && h < d.H && ww >= 0 && ww < d.W;
-                ra[i] = ok ? ldf(x + xb[i] + ((long long)h * d.W + ww) * d.C + c) : 0.f;
+                bool ok = c < d.Cg && h >= 0 && h < d.H && ww >= 0 && ww < d.W;
+                ra[i] = ok ? ldf(x + xb[i] + ((long long)h * d.W + ww) * d.C + cx0 + c) : 0.f;
             }
         } else {
             int h = hb[0] + r * d.dh, ww = wb[0] + s * d.dw;
@@ -191,8 +198,8 @@ struct FwdLoader {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 int c = c0 + t / 128 + 2 * i;
-                bool ok = okp && c < d.C;
-                ra[i] = ok ? ldf(x + xb[0] + ((long long)c * d.H + h) * d.W + ww) : 0.f;
+                bool ok = okp && c < d.Cg;
+                ra[i] = ok ? ldf(x + xb[0] + ((long long)(cx0 + c) * d.H + h) * d.W + ww) : 0.f;
             }
         }
     }
@@ -202,10 +209,11 @@ struct FwdLoader {
         const int c = c0 + t % 16;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            int k = n0 + t / 16 + 16 * i;
-            bool ok = c < d.C && k < d.K;
-            long long off = NHWC ? (((long long)k * d.R + r) * d.S + s) * d.C + c
-                                 : (((long long)k * d.C + c) * d.R + r) * d.S + s;
+            int kl = n0 + t / 16 + 16 * i;  // output channel within the group
+            bool ok = c < d.Cg && kl < d.Kg;
+            long long k = k0g + kl;
+            long long off = NHWC ? ((k * d.R + r) * d.S + s) * d.Cg + c
+                                 : ((k * d.Cg + c) * d.R + r) * d.S + s;
             rb[i] = ok ? ldf(w + off) : 0.f;
         }
     }
@@ -221,8 +229,9 @@ struct FwdLoader {
             int n = (int)(rr / d.P);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                int k = n0 + tn * 4 + j;
-                if (k >= d.K) continue;
+                int kl = n0 + tn * 4 + j;
+                if (kl >= d.Kg) continue;
+                const int k = k0g + kl;
                 float v = acc[i][j];
                 long long off = NHWC ? m * d.K + k : (((long long)n * d.K + k) * d.P + p) * d.Q + q;
                 if (alpha) v = v * alpha[k];
@@ -439,10 +448,12 @@ template <typename Ti, typename To>
 gbconv_status_t fwd_typed(const Dims &d, const void *x, const void *w, const float *bias, void *y,
                           cudaStream_t st, const Fused &fz) {
     long long M = d.M();
-    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((d.K + BN - 1) / BN), 1);
+    const int Kg = d.K / d.G, Cg = d.C / d.G;
+    if (d.G > 65535) return GBCONV_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((Kg + BN - 1) / BN), (unsigned)d.G);
     int relu = (d.flags & GBCONV_FLAG_RELU) ? 1 : 0;
     const float *b = (d.flags & GBCONV_FLAG_BIAS) ? bias : nullptr;
-    int cb = (d.C + BK - 1) / BK;
+    int cb = (Cg + BK - 1) / BK;
     if (d.layout == GBCONV_NHWC) {
         FwdLoader<Ti, To, true> L{to_k(d), (const Ti *)x, (const Ti *)w, b, (To *)y, relu, cb,
                                   fz.alpha, (const To *)fz.z};

@@ -46,7 +46,8 @@ constexpr int BM = 128;
 constexpr int A_BYTES = BM * 128;  // 128 pixels x 128 bytes of channels
 constexpr int EPI_TOTAL = EPI_TOTAL_BYTES;
 constexpr int SMEM_ALIGN = 1024;
-constexpr int BAR_BYTES = 256;
+constexpr int BAR_BYTES = 1024;
+constexpr int ZMAX = 4;  // fused residual: TMA-loaded chunks per epilogue warp and tile
 constexpr int SMEM_LIMIT = 227 * 1024;
 constexpr int GMAX = 64;  // problems per grouped launch
 
@@ -74,6 +75,8 @@ struct FwdParams {
     int raster;
     const float *alpha;  // fused epilogue of a single problem (G == 1): per-channel scale
     const void *z;       // and residual; null otherwise
+    CUtensorMap tmZ;     // residual as y's store map (BF16 output): loaded into the staging
+    int z_tma;           // buffers by TMA ahead of the accumulator when set
     Guard guard;
 };
 
@@ -106,10 +109,14 @@ __device__ __forceinline__ void decode(const FwdParams<G> &prm, int tile, int &g
     }
 }
 
-// FUSED: the epilogue also applies the per-channel scale and the residual
-// (single-problem launches only).
-template <int BN, bool FP8, int G, bool FUSED = false>
+// FMODE (single-problem launches only): 0 plain epilogue; 1 fused per-channel
+// scale and residual read by the epilogue threads (FP32 output, or no
+// residual); 2 fused with the residual tiles brought into the staging
+// buffers by TMA ahead of the accumulator (BF16 output).
+template <int BN, bool FP8, int G, int FMODE = 0>
 __global__ void __launch_bounds__(EpiShape<BN>::threads, 1) tc_fwd_kernel(const __grid_constant__ FwdParams<G> prm) {
+    constexpr bool FUSED = FMODE != 0;
+    constexpr bool ZT = FMODE == 2;
     constexpr int EPI_WARPS = EpiShape<BN>::warps;
     constexpr int EPI_BYTES = EpiShape<BN>::warp_bytes;
     constexpr int EPI_GROUPS = EPI_WARPS / 4;  // warps per TMEM lane quarter
@@ -131,7 +138,8 @@ __global__ void __launch_bounds__(EpiShape<BN>::threads, 1) tc_fwd_kernel(const 
     uint64_t *tfull = bars + 2 * stages;  // [2]
     uint64_t *tempty = tfull + 2;         // [2]
     uint64_t *done = tempty + 2;          // [1]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *zbar = done + 1;            // [EPI_WARPS][ZMAX] fused residual loads
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(zbar + EPI_WARPS * ZMAX);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -147,6 +155,8 @@ __global__ void __launch_bounds__(EpiShape<BN>::threads, 1) tc_fwd_kernel(const 
             ptx::mbar_init(&tempty[i], EPI_WARPS);
         }
         ptx::mbar_init(done, 1);
+        if (FUSED)
+            for (int i = 0; i < EPI_WARPS * ZMAX; ++i) ptx::mbar_init(&zbar[i], 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -302,14 +312,65 @@ __global__ void __launch_bounds__(EpiShape<BN>::threads, 1) tc_fwd_kernel(const 
         uint8_t *sbuf = sEpi + ew * EPI_BYTES;
         int ebuf = 0;
         int local = 0;
+        uint32_t zbits = 0;  // phase of each residual slot's barrier
+        uint32_t zdrain = 0, zdpar = 0;  // slots (and phases) an abort left in flight
         for (int tile = blockIdx.x; tile < prm.num_tiles; tile += gridDim.x, ++local) {
             int g, mt, nt;
             decode(prm, tile, g, mt, nt);
             const ProbArgs &pa = prm.pa[g];
             const int acc = local & 1;
             const uint32_t aph = (local >> 1) & 1;
+            uint32_t zmask = 0, zpar = 0;  // residual slots loaded for this tile, their phases
+            if constexpr (FUSED && G == 1) {
+                if (ZT) {
+                    // residual chunks of this warp -> its staging buffers, by TMA, while
+                    // the MMAs run (the buffers' previous stores must have been read)
+                    if (lane == 0) {
+                        // the next tile's residual chunks into L2 meanwhile
+                        const int t2 = tile + (int)gridDim.x;
+                        if (t2 < prm.num_tiles) {
+                            int g2, mt2, nt2;
+                            decode(prm, t2, g2, mt2, nt2);
+                            for (int j = half; j < pa.bn / 32; j += EPI_GROUPS) {
+                                const int c0z = nt2 * pa.bn + j * 32, r0z = mt2 * BM + quarter * 32;
+                                if (c0z < pa.K && r0z < pa.M) ptx::tma_prefetch_2d(&prm.tmZ, c0z, r0z);
+                            }
+                        }
+                        ptx::bulk_wait_read<0>();
+                    }
+                    for (int j = half, ci = 0; j < pa.bn / 32; j += EPI_GROUPS, ++ci) {
+                        const int c0z = nt * pa.bn + j * 32, r0z = mt * BM + quarter * 32;
+                        if (c0z >= pa.K || r0z >= pa.M) continue;
+                        zmask |= 1u << ci;
+                        if (lane == 0) {
+                            ptx::mbar_arrive_expect_tx(&zbar[ew * ZMAX + ci], 2048);
+                            ptx::tma_load_2d(sbuf + ci * 2048, &prm.tmZ, &zbar[ew * ZMAX + ci], c0z,
+                                             r0z);
+                        }
+                    }
+                    zpar = zbits;
+                    zbits ^= zmask;
+                    __syncwarp();
+                } else if (prm.z) {
+                    // residual rows of this warp's chunks into L2, one tile ahead (the
+                    // first tile's at the start): they arrive while the MMAs run
+                    const EpiArgs ea{pa.K, 0, pa.out_f32, nullptr, nullptr, nullptr, prm.z,
+                                     (long long)pa.M, pa.Q};
+                    for (int t2 = (local == 0 ? tile : tile + (int)gridDim.x);
+                         t2 <= tile + (int)gridDim.x && t2 < prm.num_tiles; t2 += (int)gridDim.x) {
+                        int g2, mt2, nt2;
+                        decode(prm, t2, g2, mt2, nt2);
+                        for (int j = half; j < pa.bn / 32; j += EPI_GROUPS)
+                            prefetch_residual(ea, nt2 * pa.bn + j * 32, mt2 * BM + quarter * 32, -1,
+                                              lane);
+                    }
+                }
+            }
+
             if (!ptx::mbar_wait(&tfull[acc], aph, lim, abort_flag)) {
                 fail();
+                zdrain = zmask;  // residual loads of this tile still to land
+                zdpar = zpar;
                 break;
             }
             ptx::tc_fence_after();
@@ -331,17 +392,34 @@ __global__ void __launch_bounds__(EpiShape<BN>::threads, 1) tc_fwd_kernel(const 
                 }
                 const int col0 = nt * pa.bn + j * 32;
                 if (col0 >= pa.K || row0 >= pa.M) continue;  // chunk entirely outside y
-                epilogue_chunk<FP8, EpiShape<BN>::nbuf, FUSED>(v, EpiArgs{pa.K, pa.relu, pa.out_f32, pa.bias, pa.w_scale,
-                                                                    G == 1 ? prm.alpha : nullptr,
-                                                                    G == 1 ? prm.z : nullptr,
-                                                                    (long long)pa.M, pa.Q},
-                                    &prm.tmY[g], xs, col0, row0, -1, lane, sbuf, ebuf);
+                const EpiArgs ea{pa.K, pa.relu, pa.out_f32, pa.bias, pa.w_scale,
+                                 G == 1 ? prm.alpha : nullptr, G == 1 ? prm.z : nullptr,
+                                 (long long)pa.M, pa.Q};
+                if constexpr (ZT) {
+                    const int ci = (j - half) / EPI_GROUPS;
+                    if (!((zmask >> ci) & 1u)) continue;
+                    if (!ptx::mbar_wait(&zbar[ew * ZMAX + ci], (zpar >> ci) & 1u, lim, abort_flag)) {
+                        fail();
+                        continue;
+                    }
+                    epilogue_chunk_zsmem<FP8>(v, ea, &prm.tmY[g], xs, col0, row0, -1, lane,
+                                              sbuf + ci * 2048);
+                } else {
+                    epilogue_chunk<FP8, EpiShape<BN>::nbuf, FUSED>(v, ea, &prm.tmY[g], xs, col0, row0,
+                                                                   -1, lane, sbuf, ebuf);
+                }
             }
             if (!released) {
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
             }
+        }
+        if (FUSED && zdrain && lane == 0) {
+            // an aborted tile's residual loads must land before the CTA leaves
+            volatile int zero = 0;
+            for (int ci = 0; ci < ZMAX; ++ci)
+                if ((zdrain >> ci) & 1u) ptx::mbar_wait(&zbar[ew * ZMAX + ci], (zdpar >> ci) & 1u, lim, &zero);
         }
         if (lane == 0) ptx::bulk_wait<0>();  // stores done before the CTA leaves
     }
@@ -370,24 +448,24 @@ size_t smem_bytes(int bn, int stages) {
     return (size_t)SMEM_ALIGN + (size_t)stages * (A_BYTES + bn * 128) + EPI_TOTAL + BAR_BYTES;
 }
 
-template <int BN, bool FP8, int G, bool FUSED = false>
+template <int BN, bool FP8, int G, int FMODE = 0>
 gbconv_status_t launch_kernel(const FwdParams<G> &prm, int grid, cudaStream_t st) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(tc_fwd_kernel<BN, FP8, G, FUSED>,
+        attr_err = cudaFuncSetAttribute(tc_fwd_kernel<BN, FP8, G, FMODE>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
     });
     if (attr_err != cudaSuccess) return cuda_status(attr_err);
     size_t smem = smem_bytes(BN, prm.stages);
-    return cuda_status(launch_pdl(tc_fwd_kernel<BN, FP8, G, FUSED>, dim3(grid),
+    return cuda_status(launch_pdl(tc_fwd_kernel<BN, FP8, G, FMODE>, dim3(grid),
                                   dim3(EpiShape<BN>::threads), smem, st, prm));
 }
 
-template <int BN, bool FUSED>
+template <int BN, int FMODE>
 gbconv_status_t launch_single(const FwdParams<1> &prm, bool fp8, int grid, cudaStream_t st) {
-    return fp8 ? launch_kernel<BN, true, 1, FUSED>(prm, grid, st)
-               : launch_kernel<BN, false, 1, FUSED>(prm, grid, st);
+    return fp8 ? launch_kernel<BN, true, 1, FMODE>(prm, grid, st)
+               : launch_kernel<BN, false, 1, FMODE>(prm, grid, st);
 }
 
 // Fills pa, tmA, tmB for one problem; bn is the tile width used.
@@ -405,7 +483,7 @@ gbconv_status_t setup_problem(const Dims &d, int bn, const void *x, const void *
     gbconv_status_t s;
     if (a_tiled) {
         uint64_t adims[2] = {(uint64_t)d.C, (uint64_t)d.M()};
-        uint64_t astr[1] = {(uint64_t)d.C * eb};
+        uint64_t astr[1] = {(uint64_t)d.xstride() * eb};
         uint32_t abox[2] = {(uint32_t)ke, (uint32_t)BM};
         s = encode_tiled(&ta, in_t, 2, x, adims, astr, abox, CU_TENSOR_MAP_SWIZZLE_128B);
     } else {
@@ -415,7 +493,7 @@ gbconv_status_t setup_problem(const Dims &d, int bn, const void *x, const void *
     // y [M][K]: stored in 32-row x 32-column chunks (BF16: 64-byte rows, FP32: 128-byte rows)
     const bool of32 = d.out_dtype == GBCONV_F32;
     uint64_t ydims[2] = {(uint64_t)d.K, (uint64_t)d.M()};
-    uint64_t ystr[1] = {(uint64_t)d.K * (of32 ? 4 : 2)};
+    uint64_t ystr[1] = {(uint64_t)d.ystride() * (of32 ? 4 : 2)};
     uint32_t ybox[2] = {32, 32};
     s = encode_tiled(&ty, of32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                      2, y, ydims, ystr, ybox,
@@ -530,23 +608,40 @@ gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void 
     prm.raster = cfg.raster;
     prm.alpha = fz.alpha;
     prm.z = fz.z;
+    if (fz.z && d.out_dtype == GBCONV_BF16) {  // residual tiles by TMA, y's store map shape
+        uint64_t zd[2] = {(uint64_t)d.K, (uint64_t)d.M()};
+        uint64_t zs[1] = {(uint64_t)d.ystride() * 2};
+        uint32_t zb[2] = {32, 32};
+        s = encode_tiled(&prm.tmZ, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, fz.z, zd, zs, zb,
+                         CU_TENSOR_MAP_SWIZZLE_64B);
+        if (s != GBCONV_OK) return s;
+        prm.z_tma = 1;
+    }
     prm.guard = make_guard();
     if (!prm.guard.err) return GBCONV_ERR_CUDA;
     int grid = std::min(prm.num_tiles, sm_count());
     const bool fp8 = d.in_dtype == GBCONV_E4M3;
+    if (prm.z_tma) {
+        switch (cfg.block_n) {
+            case 32: return launch_single<32, 2>(prm, fp8, grid, st);
+            case 64: return launch_single<64, 2>(prm, fp8, grid, st);
+            case 128: return launch_single<128, 2>(prm, fp8, grid, st);
+            default: return launch_single<256, 2>(prm, fp8, grid, st);
+        }
+    }
     if (fz.alpha || fz.z) {
         switch (cfg.block_n) {
-            case 32: return launch_single<32, true>(prm, fp8, grid, st);
-            case 64: return launch_single<64, true>(prm, fp8, grid, st);
-            case 128: return launch_single<128, true>(prm, fp8, grid, st);
-            default: return launch_single<256, true>(prm, fp8, grid, st);
+            case 32: return launch_single<32, 1>(prm, fp8, grid, st);
+            case 64: return launch_single<64, 1>(prm, fp8, grid, st);
+            case 128: return launch_single<128, 1>(prm, fp8, grid, st);
+            default: return launch_single<256, 1>(prm, fp8, grid, st);
         }
     }
     switch (cfg.block_n) {
-        case 32: return launch_single<32, false>(prm, fp8, grid, st);
-        case 64: return launch_single<64, false>(prm, fp8, grid, st);
-        case 128: return launch_single<128, false>(prm, fp8, grid, st);
-        default: return launch_single<256, false>(prm, fp8, grid, st);
+        case 32: return launch_single<32, 0>(prm, fp8, grid, st);
+        case 64: return launch_single<64, 0>(prm, fp8, grid, st);
+        case 128: return launch_single<128, 0>(prm, fp8, grid, st);
+        default: return launch_single<256, 0>(prm, fp8, grid, st);
     }
 }
 

@@ -329,14 +329,28 @@ __global__ void __launch_bounds__(EpiShape<BN>::threads, 1)
             sdecode(prm, tile, n, p0, nt);
             const int acc = local & 1;
             const uint32_t aph = (local >> 1) & 1;
+            const int p = p0 + ((quarter * 32) >> prm.wx_log2);
+            const int q0 = (quarter * 32) & wx_mask;
+            const bool rows_ok = p < prm.P && q0 < prm.Q;
+            if constexpr (FUSED) {  // residual rows into L2, this tile (first) and the next
+                if (prm.epi.z)
+                    for (int t2 = (local == 0 ? tile : tile + (int)gridDim.x);
+                         t2 <= tile + (int)gridDim.x && t2 < prm.num_tiles; t2 += (int)gridDim.x) {
+                        int n2, p02, nt2;
+                        sdecode(prm, t2, n2, p02, nt2);
+                        const int pp = p02 + ((quarter * 32) >> prm.wx_log2);
+                        const int qq = (quarter * 32) & wx_mask;
+                        if (pp < prm.P && qq < prm.Q)
+                            for (int j = half; j < prm.bn / 32; j += EPI_GROUPS)
+                                prefetch_residual(prm.epi, nt2 * prm.bn + j * 32, qq, n2 * prm.P + pp,
+                                                  lane);
+                    }
+            }
             if (!ptx::mbar_wait(&tfull[acc], aph, lim, abort_flag)) {
                 fail();
                 break;
             }
             ptx::tc_fence_after();
-            const int p = p0 + ((quarter * 32) >> prm.wx_log2);
-            const int q0 = (quarter * 32) & wx_mask;
-            const bool rows_ok = p < prm.P && q0 < prm.Q;
             const float xs = FP8 ? __ldg(prm.x_scale) : 1.f;
             const int nchunks = prm.bn / 32;
             bool released = false;

@@ -476,6 +476,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                         as[h][s2] = (FUSED && prm.alpha && k < prm.K) ? __ldg(prm.alpha + k) : 1.f;
                     }
             }
+            if constexpr (FUSED) {  // residual of this warp's chunks into L2: lane = position
+                if (prm.z) {
+                    const int eb = prm.out_f32 ? 4 : 2;
+                    const int kw0 = kt * KT + chb0;
+                    for (int j = group; j < nchunks && kw0 < prm.K; j += EPI_GROUPS) {
+                        size_t row;
+                        bool ok;
+                        if (prm.flat) {
+                            row = (size_t)p0 + 32 * j + lane;
+                            ok = row < (size_t)prm.M;
+                        } else {
+                            const int p = p0 + ((32 * j) >> prm.wx_log2);
+                            const int q = ((32 * j) & wx_mask) + lane;
+                            ok = p < T.P && q < T.Q;
+                            row = ((size_t)n * prm.out_H + (size_t)p * prm.ou + T.oa) * prm.out_W +
+                                  T.ob + (size_t)q * prm.ov;
+                        }
+                        if (ok)
+                            ptx::prefetch_l2(static_cast<const char *>(prm.z) +
+                                             (row * prm.K + kw0) * eb);
+                    }
+                }
+            }
             if (!ptx::mbar_wait(&tfull[acc], aph, lim, abort_flag)) {
                 fail();
                 break;

@@ -47,9 +47,10 @@ gbconv_status_t encode_im2col_act(CUtensorMap *m, const Dims &d, const void *x, 
     std::call_once(g_once, load_entry_points);
     if (!g_im2col) return GBCONV_ERR_CUDA;
     if (reinterpret_cast<uintptr_t>(x) % 16) return GBCONV_ERR_ALIGNMENT;
+    const cuuint64_t ldc = (cuuint64_t)d.xstride();  // channels between pixels
     cuuint64_t dims[4] = {(cuuint64_t)d.C, (cuuint64_t)d.W, (cuuint64_t)d.H, (cuuint64_t)d.N};
-    cuuint64_t strides[3] = {(cuuint64_t)d.C * elem_bytes, (cuuint64_t)d.W * d.C * elem_bytes,
-                             (cuuint64_t)d.H * d.W * d.C * elem_bytes};
+    cuuint64_t strides[3] = {ldc * elem_bytes, (cuuint64_t)d.W * ldc * elem_bytes,
+                             (cuuint64_t)d.H * d.W * ldc * elem_bytes};
     int lower[2] = {-d.pw, -d.ph};
     int upper[2] = {d.pw - d.dw * (d.S - 1), d.ph - d.dh * (d.R - 1)};
     cuuint32_t estr[4] = {1, (cuuint32_t)d.v, (cuuint32_t)d.u, 1};

@@ -28,7 +28,7 @@ def _check_dev(*ts):
 
 
 def make_problem(x, w, stride=1, padding=0, dilation=1, layout="NHWC", out_dtype=None,
-                 bias=False, relu=False):
+                 bias=False, relu=False, groups=1):
     lay = B.GBCONV_NHWC if layout == "NHWC" else B.GBCONV_NCHW
     if layout == "NHWC":
         N, H, W, C = x.shape
@@ -36,13 +36,13 @@ def make_problem(x, w, stride=1, padding=0, dilation=1, layout="NHWC", out_dtype
     else:
         N, C, H, W = x.shape
         K, C2, R, S = w.shape
-    if C != C2:
-        raise ValueError(f"channel mismatch: x has {C}, w has {C2}")
+    if C != C2 * groups:
+        raise ValueError(f"channel mismatch: x has {C}, w has {C2} per group x {groups} groups")
     ind = _DT[x.dtype]
     outd = _DT[out_dtype] if out_dtype is not None else (B.GBCONV_BF16 if ind == B.GBCONV_E4M3 else ind)
     flags = (B.GBCONV_FLAG_BIAS if bias else 0) | (B.GBCONV_FLAG_RELU if relu else 0)
     return B.problem(N, C, H, W, K, R, S, _pair(stride), _pair(padding), _pair(dilation), ind,
-                     outd, lay, flags)
+                     outd, lay, flags, groups)
 
 
 def out_shape(prob, layout):
@@ -52,11 +52,13 @@ def out_shape(prob, layout):
 
 
 def conv2d(x, w, bias=None, stride=1, padding=0, dilation=1, relu=False, layout="NHWC",
-           out_dtype=None, x_scale=None, w_scale=None, out=None):
+           out_dtype=None, x_scale=None, w_scale=None, out=None, groups=1):
     """Forward convolution through conv2d_fwd. For E4M3 inputs pass the fp32
-    scales (x_scale: 1 element, w_scale: K elements) from quantize_e4m3."""
+    scales (x_scale: 1 element, w_scale: K elements) from quantize_e4m3.
+    groups > 1: channel groups (w holds C/groups channels per output channel)."""
     _check_dev(x, w, bias, x_scale, w_scale)
-    prob = make_problem(x, w, stride, padding, dilation, layout, out_dtype, bias is not None, relu)
+    prob = make_problem(x, w, stride, padding, dilation, layout, out_dtype, bias is not None, relu,
+                        groups)
     if out is None:
         out = torch.empty(out_shape(prob, layout), dtype=_TORCH[prob.out_dtype], device=x.device)
     s = B.conv2d_fwd(prob, x.data_ptr(), w.data_ptr(), bias.data_ptr() if bias is not None else 0,
@@ -68,12 +70,14 @@ def conv2d(x, w, bias=None, stride=1, padding=0, dilation=1, relu=False, layout=
 
 
 def conv2d_fused(x, w, bias=None, scale=None, residual=None, stride=1, padding=0, dilation=1,
-                 relu=False, layout="NHWC", out_dtype=None, x_scale=None, w_scale=None, out=None):
+                 relu=False, layout="NHWC", out_dtype=None, x_scale=None, w_scale=None, out=None,
+                 groups=1):
     """y = act(scale[k] * conv(x, w) + bias[k] + residual) through
     conv2d_fwd_fused (batch normalisation folded into scale/bias with
     bn_fold; residual of y's shape and dtype, may be ``out`` itself)."""
     _check_dev(x, w, bias, scale, residual, x_scale, w_scale)
-    prob = make_problem(x, w, stride, padding, dilation, layout, out_dtype, bias is not None, relu)
+    prob = make_problem(x, w, stride, padding, dilation, layout, out_dtype, bias is not None, relu,
+                        groups)
     if out is None:
         out = torch.empty(out_shape(prob, layout), dtype=_TORCH[prob.out_dtype], device=x.device)
     ptr = lambda t: t.data_ptr() if t is not None else 0
