@@ -67,6 +67,14 @@ def _load():
             lib.oracle_bn_fold.argtypes = [ctypes.c_int64, _f64p, _f64p, _f64p, _f64p,
                                            ctypes.c_double, _f64p, _f64p, _f64p]
             lib.oracle_bn_fold.restype = None
+            lib.oracle_nll_loss_fwd.argtypes = [_f64p, _i64p, _f64p, ctypes.c_int64,
+                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                                _f64p, _f64p]
+            lib.oracle_nll_loss_bwd.argtypes = [_f64p, _i64p, _f64p, ctypes.c_int64,
+                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                                ctypes.c_double, _f64p]
+            lib.oracle_nll_loss_fwd.restype = ctypes.c_int
+            lib.oracle_nll_loss_bwd.restype = ctypes.c_int
             lib.oracle_round_bf16.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
             lib.oracle_bf16_to_f64.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
             lib.oracle_quant_e4m3.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
@@ -301,3 +309,42 @@ def max_normalised_error(got, ref, bound) -> float:
     if got.size == 0:
         return 0.0
     return float(np.max(np.abs(got - ref) / bound))
+
+
+# ---- negative log-likelihood loss (Sec. 5.B) ----
+
+NLL_REDUCTIONS = {"none": 0, "mean": 1, "sum": 2}
+
+
+def nll_loss(logp, target, weight=None, ignore_index=-100, reduction="mean"):
+    """The ClassNLLCriterion forward in float64: returns (out, total_weight);
+    out has N values for reduction 'none', else one."""
+    lp = _f64(logp)
+    N, C = lp.shape
+    t = np.ascontiguousarray(np.asarray(target, dtype=np.int64))
+    wt = _f64(weight) if weight is not None else None
+    red = NLL_REDUCTIONS[reduction]
+    out = np.empty(N if red == 0 else 1)
+    tw = np.empty(1)
+    rc = _load().oracle_nll_loss_fwd(_ptr(lp, _f64p), _ptr(t, _i64p),
+                                     _ptr(wt, _f64p) if wt is not None else None, N, C,
+                                     int(ignore_index), red, _ptr(out, _f64p), _ptr(tw, _f64p))
+    if rc:
+        raise ValueError("target outside [0, C) and not ignore_index")
+    return out, float(tw[0])
+
+
+def nll_loss_grad(grad_out, target, N, C, weight=None, ignore_index=-100, reduction="mean",
+                  total_weight=1.0):
+    """The ClassNLLCriterion gradient with respect to logp, [N][C] float64."""
+    g = _f64(np.atleast_1d(grad_out))
+    t = np.ascontiguousarray(np.asarray(target, dtype=np.int64))
+    wt = _f64(weight) if weight is not None else None
+    out = np.empty((N, C))
+    rc = _load().oracle_nll_loss_bwd(_ptr(g, _f64p), _ptr(t, _i64p),
+                                     _ptr(wt, _f64p) if wt is not None else None, N, C,
+                                     int(ignore_index), NLL_REDUCTIONS[reduction],
+                                     float(total_weight), _ptr(out, _f64p))
+    if rc:
+        raise ValueError("target outside [0, C) and not ignore_index")
+    return out

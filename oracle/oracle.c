@@ -460,3 +460,56 @@ void oracle_scale_quant_e4m3(const float *in, int64_t rows, int64_t len, uint8_t
         }
     }
 }
+
+/* ---- negative log-likelihood loss (Sec. 5.B: the ClassNLLCriterion forward
+ * and gradient that ResNet-50 training calls after the network) ----
+ *
+ * logp is [N][C] (log-probabilities), target[n] a class index or ignore_index,
+ * weight[c] an optional class weight (NULL: 1). With w_n = weight[target[n]]
+ * for counted rows and 0 for ignored ones:
+ *   reduction 0 (none): out[n] = -w_n * logp[n][target[n]]
+ *   reduction 2 (sum):  out    = sum_n -w_n * logp[n][target[n]]
+ *   reduction 1 (mean): out    = (sum_n -w_n * logp[n][target[n]]) / sum_n w_n
+ * total_weight = sum_n w_n. The gradient with respect to logp for the
+ * upstream gradient g (one value, or N values for reduction none) is zero
+ * except at (n, target[n]) of counted rows: -w_n * g (none: g[n]; sum: g;
+ * mean: g / total_weight). Returns -3 if a target is neither a class nor
+ * ignore_index. */
+int oracle_nll_loss_fwd(const double *logp, const int64_t *target, const double *weight,
+                        int64_t N, int64_t C, int64_t ignore_index, int reduction, double *out,
+                        double *total_weight) {
+    double sum = 0.0, tw = 0.0;
+    for (int64_t n = 0; n < N; ++n) {
+        const int64_t t = target[n];
+        if (t == ignore_index) {
+            if (reduction == 0) out[n] = 0.0;
+            continue;
+        }
+        if (t < 0 || t >= C) return -3;
+        const double w = weight ? weight[t] : 1.0;
+        const double v = -w * logp[n * C + t];
+        if (reduction == 0) out[n] = v;
+        sum += v;
+        tw += w;
+    }
+    if (reduction == 1) out[0] = sum / tw;
+    if (reduction == 2) out[0] = sum;
+    *total_weight = tw;
+    return 0;
+}
+
+int oracle_nll_loss_bwd(const double *grad_out, const int64_t *target, const double *weight,
+                        int64_t N, int64_t C, int64_t ignore_index, int reduction,
+                        double total_weight, double *grad_in) {
+    for (int64_t i = 0; i < N * C; ++i) grad_in[i] = 0.0;
+    for (int64_t n = 0; n < N; ++n) {
+        const int64_t t = target[n];
+        if (t == ignore_index) continue;
+        if (t < 0 || t >= C) return -3;
+        const double w = weight ? weight[t] : 1.0;
+        const double g = reduction == 0 ? grad_out[n]
+                         : reduction == 1 ? grad_out[0] / total_weight : grad_out[0];
+        grad_in[n * C + t] = -w * g;
+    }
+    return 0;
+}

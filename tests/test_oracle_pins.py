@@ -516,3 +516,42 @@ def test_groups_adjoint_identities():
 def test_groups_must_divide_channels():
     with pytest.raises(ValueError):
         Conv(1, 6, 5, 5, 4, 3, 3, groups=4)
+
+
+# ---- negative log-likelihood loss ----
+
+@pytest.mark.parametrize("reduction", ["none", "mean", "sum"])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_nll_loss_matches_torch_library(reduction, weighted):
+    """Forward and gradient against PyTorch's float64 nll_loss and its autograd,
+    with ignored rows."""
+    r = _rng(31)
+    N, C = 37, 11
+    logp = torch.log_softmax(torch.from_numpy(r.normal(size=(N, C))), dim=1).requires_grad_()
+    t = torch.from_numpy(r.integers(0, C, N))
+    t[[3, 10, 20]] = -100
+    w = torch.from_numpy(r.uniform(0.5, 2.0, C)) if weighted else None
+    ref = torch.nn.functional.nll_loss(logp, t, weight=w, ignore_index=-100, reduction=reduction)
+    g = torch.from_numpy(r.normal(size=tuple(ref.shape)))
+    (ref * g).sum().backward()
+    out, tw = oracle.nll_loss(logp.detach().numpy(), t.numpy(), w.numpy() if weighted else None,
+                              -100, reduction)
+    assert np.max(np.abs(out.reshape(ref.shape) - ref.detach().numpy())) < 1e-12
+    gi = oracle.nll_loss_grad(g.numpy(), t.numpy(), N, C, w.numpy() if weighted else None, -100,
+                              reduction, tw)
+    assert np.max(np.abs(gi - logp.grad.numpy())) < 1e-12
+
+
+def test_nll_loss_worked_example():
+    """Two rows, three classes, by hand: -(log 0.5 + 2 log 0.25) / (1 + 2)."""
+    logp = np.log(np.array([[0.5, 0.25, 0.25], [0.25, 0.25, 0.5]]))
+    out, tw = oracle.nll_loss(logp, [0, 1], weight=[1.0, 2.0, 3.0], reduction="mean")
+    assert tw == 3.0 and abs(out[0] - (-(np.log(0.5) + 2 * np.log(0.25)) / 3)) < 1e-15
+    gi = oracle.nll_loss_grad([1.0], [0, 1], 2, 3, [1.0, 2.0, 3.0], reduction="mean",
+                              total_weight=tw)
+    assert np.array_equal(gi, np.array([[-1 / 3, 0, 0], [0, -2 / 3, 0]]))
+
+
+def test_nll_loss_rejects_bad_targets():
+    with pytest.raises(ValueError):
+        oracle.nll_loss(np.zeros((2, 3)), [0, 3])
