@@ -286,7 +286,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline BF16 layer set (skip FP32/FP8/grouped/backward)")
-    ap.add_argument("--sections", default="fp32,fp8,grouped,backward,fused,groups",
+    ap.add_argument("--sections", default="fp32,fp8,grouped,backward,fused,groups,nll",
                     help="comma list of extra workloads to run after the headline layer set")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     args = ap.parse_args()
@@ -367,7 +367,8 @@ def run_ours(args, rank, world, local):
     if not args.no_extras:
         sections = [x for x in args.sections.split(",") if x]
         fns = {"fp32": bench_fp32, "fp8": bench_fp8, "grouped": bench_grouped,
-               "backward": bench_backward, "fused": bench_fused, "groups": bench_groups}
+               "backward": bench_backward, "fused": bench_fused, "groups": bench_groups,
+               "nll": bench_nll}
         for name in sections:
             try:
                 out[name] = fns[name](torch, dev, args, dist_on, pk)
@@ -697,6 +698,43 @@ def bench_groups(torch, dev, args, dist_on, pk):
                     "tflops": round(flops / (us * 1e-6) / 1e12, 2),
                     "gbs": round(nbytes / (us * 1e-6) / 1e9, 1),
                     "frac_of_hbm": round(nbytes / (us * 1e-6) / 1e9 / pk["hbm_gbs"], 3)})
+    return out
+
+
+def bench_nll(torch, dev, args, dist_on, pk):
+    """Negative log-likelihood loss after a 1000-class classifier: forward
+    (two-pass reduction) and gradient, batch 32 (the ResNet-50 workload) and
+    a 65536-row batch (memory-bound: [N][C] read once, written once)."""
+    from paper_2207_00257_gb300 import binding as B
+    out = []
+    for N in (32, 65536):
+        C = 1000
+        g = torch.Generator().manual_seed(10)
+        logp = torch.log_softmax(torch.randn(N, C, generator=g), dim=1).to(dev)
+        t = torch.randint(0, C, (N,), generator=g).to(dev)
+        o = torch.empty(1, device=dev)
+        tw = torch.empty(1, device=dev)
+        go = torch.ones(1, device=dev)
+        gi = torch.empty(N, C, device=dev)
+        _, nb = B.gbconv_nll_workspace_size(N)
+        ws = torch.empty(max(nb, 4), dtype=torch.uint8, device=dev)
+
+        def fwd(i, stream, logp=logp, t=t, o=o, tw=tw, ws=ws, nb=nb, N=N):
+            B.check(B.gbconv_nll_loss_fwd(logp.data_ptr(), t.data_ptr(), 0, N, C, -100, 1,
+                                          o.data_ptr(), tw.data_ptr(), ws.data_ptr(), nb, stream),
+                    "nll fwd")
+
+        def bwd(i, stream, t=t, tw=tw, go=go, gi=gi, N=N):
+            B.check(B.gbconv_nll_loss_bwd(go.data_ptr(), t.data_ptr(), 0, N, C, -100, 1,
+                                          tw.data_ptr(), gi.data_ptr(), stream), "nll bwd")
+
+        class L:
+            def __init__(s, f):
+                s.launch = f
+        res = bench_layers([L(fwd), L(bwd)], max(3, min(args.steps, 20)), 3, 1, torch, dist_on)
+        out.append({"N": N, "C": C, "fwd_us": round(res["launch_us"][0], 2),
+                    "bwd_us": round(res["launch_us"][1], 2),
+                    "bwd_gbs": round(N * C * 4 / (res["launch_us"][1] * 1e-6) / 1e9, 1)})
     return out
 
 

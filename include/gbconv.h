@@ -67,7 +67,11 @@ typedef enum { GBCONV_OP_FWD = 0, GBCONV_OP_DGRAD = 1, GBCONV_OP_WGRAD = 2 } gbc
  * (and of g for the backward entry points); out_dtype is the type of y (or
  * dx). Supported combinations:
  *   F32  -> F32   NCHW or NHWC, any stride/pad/dilation (CUDA-core FFMA kernel)
- *   BF16 -> BF16 or F32   NHWC, C % 8 == 0, K % 8 == 0 (tensor cores, FP32 accumulate)
+ *   BF16 -> BF16 or F32   NHWC, C % 8 == 0, K % 8 == 0 (tensor cores, FP32 accumulate);
+ *                 the forward also takes BF16 NCHW (x [N,C,H,W], w [K,C,R,S], y
+ *                 [N,K,P,Q]): transpose kernels bring x and w to NHWC/KRSC in the
+ *                 workspace, the NHWC path runs, and y is transposed back
+ *                 (gbconv_workspace_size(GBCONV_OP_FWD) gives the bytes)
  *   E4M3 -> BF16  NHWC, C % 16 == 0, K % 8 == 0 (tensor cores, FP32 accumulate,
  *                 y = b + x_scale * w_scale[k] * sum(xq * wq))
  * Padding must be in [0, 127] and dilation*(R-1) <= 127 (the im2col TMA range).
@@ -140,7 +144,8 @@ gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, 
  *   x_scale: device pointer to one fp32 (E4M3 only, else ignored)
  *   w_scale: device pointer to K fp32 (E4M3 only, else ignored)
  *   y [N,P,Q,K] (NHWC) or [N,K,P,Q] (NCHW), out_dtype; must not alias x or w
- *   ws / ws_bytes: workspace (none needed; may be NULL / 0)
+ *   ws / ws_bytes: workspace: gbconv_workspace_size(GBCONV_OP_FWD) bytes, 16-byte
+ *                  aligned (only BF16 NCHW needs any; else may be NULL / 0)
  * Tensor-core paths require x, w, y 16-byte aligned. */
 gbconv_status_t conv2d_fwd(const gbconv_problem_t *prob, const void *x, const void *w,
                            const float *bias, const float *x_scale, const float *w_scale,
@@ -181,6 +186,36 @@ gbconv_status_t conv2d_fwd_fused(const gbconv_problem_t *prob, const void *x, co
 gbconv_status_t gbconv_bn_fold(int32_t K, const float *gamma, const float *bn_beta,
                                const float *mean, const float *var, float eps, const float *bias,
                                float *scale, float *shift, gbconv_stream_t stream);
+
+/* Negative log-likelihood loss (paper Sec. 5.B: ClassNLLCriterion_updateOutput
+ * and _updateGradInput, the custom CUDA kernels ResNet-50 training runs after
+ * the network; their block reduction synchronises with __syncthreads).
+ *   logp [N][C] fp32 log-probabilities; target [N] int64 class indices;
+ *   weight [C] fp32 class weights or NULL (all 1); rows whose target equals
+ *   ignore_index count with weight 0. w_n = weight[target[n]] for the others.
+ *   reduction 0 (none): out[n] = -w_n * logp[n][target[n]]  (out holds N floats)
+ *   reduction 2 (sum):  out[0] = sum_n -w_n * logp[n][target[n]]
+ *   reduction 1 (mean): out[0] = (that sum) / sum_n w_n   (NaN when every row is ignored)
+ *   total_weight[0] = sum_n w_n (all reductions; the gradient of mean needs it).
+ * All pointers are device pointers. The forward is a deterministic two-pass
+ * FP32 reduction (fixed row blocks, fixed tree order) and needs
+ * gbconv_nll_workspace_size(N) bytes of workspace. A target outside [0, C)
+ * that is not ignore_index counts as ignored and makes the next
+ * gbconv_get_device_error return GBCONV_ERR_INVALID_ARG. */
+gbconv_status_t gbconv_nll_workspace_size(int64_t N, size_t *bytes);
+gbconv_status_t gbconv_nll_loss_fwd(const float *logp, const int64_t *target, const float *weight,
+                                    int64_t N, int64_t C, int64_t ignore_index, int32_t reduction,
+                                    float *out, float *total_weight, void *ws, size_t ws_bytes,
+                                    gbconv_stream_t stream);
+/* Gradient of the loss with respect to logp, written to every element of
+ * grad_in [N][C]: -w_n * g at (n, target[n]) of counted rows, 0 elsewhere, with
+ * g = grad_out[n] (none), grad_out[0] (sum) or grad_out[0] / total_weight[0]
+ * (mean; total_weight from the forward). */
+gbconv_status_t gbconv_nll_loss_bwd(const float *grad_out, const int64_t *target,
+                                    const float *weight, int64_t N, int64_t C,
+                                    int64_t ignore_index, int32_t reduction,
+                                    const float *total_weight, float *grad_in,
+                                    gbconv_stream_t stream);
 
 /* Data gradient (paper Sec. 5.B, backward pass; the transposed convolution).
  *   dy [N,P,Q,K] or [N,K,P,Q] (in_dtype), w as in conv2d_fwd (in_dtype),

@@ -35,6 +35,7 @@ EXPORTS = [
     "gbconv_set_config", "gbconv_tune", "gbconv_tune_cache_save", "gbconv_tune_cache_load",
     "gbconv_get_device_error", "gbconv_status_string", "gbconv_debug_set", "gbconv_version",
     "gbconv_shutdown", "conv2d_dgrad_noalloc", "conv2d_fwd_fused", "gbconv_bn_fold",
+    "gbconv_nll_workspace_size", "gbconv_nll_loss_fwd", "gbconv_nll_loss_bwd",
 ]
 
 
@@ -93,6 +94,12 @@ _SIGS = {
                                         ctypes.c_size_t, _P]),
     "gbconv_bn_fold": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, ctypes.c_float, _P, _P, _P,
                                       _P]),
+    "gbconv_nll_workspace_size": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
+    "gbconv_nll_loss_fwd": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_int64, ctypes.c_int32, _P, _P, _P,
+                                           ctypes.c_size_t, _P]),
+    "gbconv_nll_loss_bwd": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_int64, ctypes.c_int32, _P, _P, _P]),
 }
 
 
@@ -169,6 +176,26 @@ def conv2d_fwd_fused(prob, x, w, bias, scale, residual, x_scale, w_scale, y, ws,
 def gbconv_bn_fold(K, gamma, bn_beta, mean, var, eps, bias, scale, shift, stream):
     return lib().gbconv_bn_fold(int(K), _vp(gamma), _vp(bn_beta), _vp(mean), _vp(var),
                                 float(eps), _vp(bias), _vp(scale), _vp(shift), _vp(stream))
+
+
+def gbconv_nll_workspace_size(N):
+    n = ctypes.c_size_t(0)
+    s = lib().gbconv_nll_workspace_size(int(N), ctypes.byref(n))
+    return s, n.value
+
+
+def gbconv_nll_loss_fwd(logp, target, weight, N, C, ignore_index, reduction, out, total_weight,
+                        ws, ws_bytes, stream):
+    return lib().gbconv_nll_loss_fwd(_vp(logp), _vp(target), _vp(weight), int(N), int(C),
+                                     int(ignore_index), int(reduction), _vp(out),
+                                     _vp(total_weight), _vp(ws), ws_bytes, _vp(stream))
+
+
+def gbconv_nll_loss_bwd(grad_out, target, weight, N, C, ignore_index, reduction, total_weight,
+                        grad_in, stream):
+    return lib().gbconv_nll_loss_bwd(_vp(grad_out), _vp(target), _vp(weight), int(N), int(C),
+                                     int(ignore_index), int(reduction), _vp(total_weight),
+                                     _vp(grad_in), _vp(stream))
 
 
 def conv2d_dgrad(prob, dy, w, dx, ws, ws_bytes, stream):

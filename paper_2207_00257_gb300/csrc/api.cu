@@ -242,9 +242,57 @@ gbconv_status_t do_fwd_groups(const Dims &d, const void *x, const void *w, const
     return launch_simt_fwd(d, x, w, bias, y, st, fz);
 }
 
+// Workspace of a BF16 NCHW forward: x as NHWC, w as KRSC, y as NHWC.
+bool nchw_bf16(const Dims &d) {
+    return d.layout == GBCONV_NCHW && d.in_dtype == GBCONV_BF16 && d.G == 1;
+}
+size_t nchw_ws_bytes(const Dims &d) {
+    const int eo = d.out_dtype == GBCONV_F32 ? 4 : 2;
+    return round256((size_t)d.N * d.H * d.W * d.C * 2) + round256((size_t)d.K * d.R * d.S * d.C * 2) +
+           round256((size_t)d.M() * d.K * eo);
+}
+
 gbconv_status_t do_fwd(const Dims &d, const TcConfig &cfg, const void *x, const void *w,
                        const float *bias, const float *x_scale, const float *w_scale, void *y,
-                       cudaStream_t st, const Fused &fz = Fused{}) {
+                       cudaStream_t st, const Fused &fz = Fused{});
+
+// BF16 NCHW forward on the NHWC tensor-core path through layout transforms
+// (a transpose kernel in front of the producer and behind the epilogue). The
+// residual, if any, is transposed into the NHWC output buffer and added in
+// place.
+gbconv_status_t do_fwd_nchw_bf16(const Dims &d, const void *x, const void *w, const float *bias,
+                                 void *y, void *ws, size_t ws_bytes, cudaStream_t st,
+                                 const Fused &fz) {
+    if (d.M() == 0) return GBCONV_OK;
+    if (!ws || ws_bytes < nchw_ws_bytes(d)) return GBCONV_ERR_WORKSPACE;
+    if (!aligned16(ws)) return GBCONV_ERR_ALIGNMENT;
+    const int eo = d.out_dtype == GBCONV_F32 ? 4 : 2;
+    char *p = static_cast<char *>(ws);
+    void *xn = p;
+    p += round256((size_t)d.N * d.H * d.W * d.C * 2);
+    void *wn = p;
+    p += round256((size_t)d.K * d.R * d.S * d.C * 2);
+    void *yn = p;
+    gbconv_status_t s = launch_transpose_b(x, xn, d.N, d.C, d.H * d.W, 2, st);  // NCHW -> NHWC
+    if (s != GBCONV_OK) return s;
+    s = launch_transpose_b(w, wn, d.K, d.C, d.R * d.S, 2, st);  // KCRS -> KRSC
+    if (s != GBCONV_OK) return s;
+    Fused f2 = fz;
+    if (fz.z) {  // residual [N][K][P*Q] -> [N][P*Q][K] in the output buffer
+        s = launch_transpose_b(fz.z, yn, d.N, d.K, d.P * d.Q, eo, st);
+        if (s != GBCONV_OK) return s;
+        f2.z = yn;
+    }
+    Dims e = d;
+    e.layout = GBCONV_NHWC;
+    s = do_fwd(e, tc_fwd_default_config(e), xn, wn, bias, nullptr, nullptr, yn, st, f2);
+    if (s != GBCONV_OK) return s;
+    return launch_transpose_b(yn, y, d.N, d.P * d.Q, d.K, eo, st);  // NHWC -> NCHW
+}
+
+gbconv_status_t do_fwd(const Dims &d, const TcConfig &cfg, const void *x, const void *w,
+                       const float *bias, const float *x_scale, const float *w_scale, void *y,
+                       cudaStream_t st, const Fused &fz) {
     if (d.M() == 0) return GBCONV_OK;
     if (d.G > 1) return do_fwd_groups(d, x, w, bias, x_scale, w_scale, y, st, fz);
     if (d.in_dtype == GBCONV_F32) {
@@ -358,7 +406,10 @@ gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, 
     if (s != GBCONV_OK) return s;
     if (!bytes) return GBCONV_ERR_INVALID_ARG;
     *bytes = 0;
-    if (op == GBCONV_OP_FWD) return GBCONV_OK;
+    if (op == GBCONV_OP_FWD) {
+        if (nchw_bf16(d)) *bytes = nchw_ws_bytes(d);
+        return GBCONV_OK;
+    }
     if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;  // grouped gradients are not implemented
     if (op == GBCONV_OP_DGRAD) {
         Dims t;
@@ -377,14 +428,15 @@ gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, 
 gbconv_status_t conv2d_fwd(const gbconv_problem_t *prob, const void *x, const void *w,
                            const float *bias, const float *x_scale, const float *w_scale, void *y,
                            void *ws, size_t ws_bytes, gbconv_stream_t stream) {
-    (void)ws;
-    (void)ws_bytes;
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
     if (d.N == 0) return GBCONV_OK;  // empty batch: nothing to read or write
     if (!x || !w || !y || ((d.flags & GBCONV_FLAG_BIAS) && !bias)) return GBCONV_ERR_INVALID_ARG;
     if (x == y || w == y) return GBCONV_ERR_INVALID_ARG;
+    if (nchw_bf16(d))
+        return do_fwd_nchw_bf16(d, x, w, bias, y, ws, ws_bytes, static_cast<cudaStream_t>(stream),
+                                Fused{});
     return do_fwd(d, config_for(GBCONV_OP_FWD, *prob, d), x, w, bias, x_scale, w_scale, y,
                   static_cast<cudaStream_t>(stream));
 }
@@ -393,8 +445,6 @@ gbconv_status_t conv2d_fwd_fused(const gbconv_problem_t *prob, const void *x, co
                                  const float *bias, const float *scale, const void *residual,
                                  const float *x_scale, const float *w_scale, void *y, void *ws,
                                  size_t ws_bytes, gbconv_stream_t stream) {
-    (void)ws;
-    (void)ws_bytes;
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
@@ -404,8 +454,44 @@ gbconv_status_t conv2d_fwd_fused(const gbconv_problem_t *prob, const void *x, co
     Fused fz;
     fz.alpha = scale;
     fz.z = residual;
+    if (nchw_bf16(d))
+        return do_fwd_nchw_bf16(d, x, w, bias, y, ws, ws_bytes, static_cast<cudaStream_t>(stream),
+                                fz);
     return do_fwd(d, config_for(GBCONV_OP_FWD, *prob, d), x, w, bias, x_scale, w_scale, y,
                   static_cast<cudaStream_t>(stream), fz);
+}
+
+gbconv_status_t gbconv_nll_workspace_size(int64_t N, size_t *bytes) {
+    if (N < 0 || !bytes) return GBCONV_ERR_INVALID_ARG;
+    *bytes = nll_workspace_bytes(N);
+    return GBCONV_OK;
+}
+
+gbconv_status_t gbconv_nll_loss_fwd(const float *logp, const int64_t *target, const float *weight,
+                                    int64_t N, int64_t C, int64_t ignore_index, int32_t reduction,
+                                    float *out, float *total_weight, void *ws, size_t ws_bytes,
+                                    gbconv_stream_t stream) {
+    if (N < 0 || C < 1 || reduction < 0 || reduction > 2 || !out || !total_weight)
+        return GBCONV_ERR_INVALID_ARG;
+    if (N > 0 && (!logp || !target)) return GBCONV_ERR_INVALID_ARG;
+    if (N * C >= (1ll << 40)) return GBCONV_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < nll_workspace_bytes(N)) return GBCONV_ERR_WORKSPACE;
+    return launch_nll_fwd(logp, target, weight, N, C, ignore_index, reduction, out, total_weight,
+                          static_cast<float *>(ws), static_cast<cudaStream_t>(stream));
+}
+
+gbconv_status_t gbconv_nll_loss_bwd(const float *grad_out, const int64_t *target,
+                                    const float *weight, int64_t N, int64_t C,
+                                    int64_t ignore_index, int32_t reduction,
+                                    const float *total_weight, float *grad_in,
+                                    gbconv_stream_t stream) {
+    if (N < 0 || C < 1 || reduction < 0 || reduction > 2) return GBCONV_ERR_INVALID_ARG;
+    if (N == 0) return GBCONV_OK;
+    if (!grad_out || !target || !grad_in || (reduction == 1 && !total_weight))
+        return GBCONV_ERR_INVALID_ARG;
+    if (N * C >= (1ll << 40)) return GBCONV_ERR_INVALID_ARG;
+    return launch_nll_grad(grad_out, target, weight, N, C, ignore_index, reduction, total_weight,
+                           grad_in, static_cast<cudaStream_t>(stream));
 }
 
 gbconv_status_t gbconv_bn_fold(int32_t K, const float *gamma, const float *bn_beta,
@@ -667,7 +753,7 @@ gbconv_status_t gbconv_get_device_error(gbconv_stream_t stream) {
         unsigned int z = 0;
         if (cudaMemcpy(di->err, &z, sizeof z, cudaMemcpyHostToDevice) != cudaSuccess)
             return GBCONV_ERR_CUDA;
-        return GBCONV_ERR_TIMEOUT;
+        return (h & DEVERR_TIMEOUT) ? GBCONV_ERR_TIMEOUT : GBCONV_ERR_INVALID_ARG;
     }
     return GBCONV_OK;
 }

@@ -142,6 +142,29 @@ __global__ void transpose_krsc(const T *__restrict__ w, T *__restrict__ wt, int 
     }
 }
 
+// Batched transpose out[b][j][i] = in[b][i][j] (in: [B][R][Cn]) through 32x32
+// shared-memory tiles (one padding column against bank conflicts): the NCHW
+// <-> NHWC and KCRS -> KRSC layout transforms around the NHWC tensor-core path.
+template <typename T>
+__global__ void transpose_b(const T *__restrict__ in, T *__restrict__ out, int R, int Cn) {
+    __shared__ T tile[32][33];
+    ptx::griddep_wait();
+    if (threadIdx.x == 0 && threadIdx.y == 0) ptx::griddep_launch();
+    const long long b = blockIdx.z;
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const T *src = in + b * (long long)R * Cn;
+    T *dst = out + b * (long long)R * Cn;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int i = i0 + k, j = j0 + threadIdx.x;
+        if (i < R && j < Cn) tile[k][threadIdx.x] = src[(long long)i * Cn + j];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int j = j0 + k, i = i0 + threadIdx.x;
+        if (i < R && j < Cn) dst[(long long)j * R + i] = tile[threadIdx.x][k];
+    }
+}
+
 // Inference batch normalisation after a convolution with bias, folded into
 // the fused forward's per-channel scale and shift (sqrtf and the division
 // are the correctly rounded FP32 operations).
@@ -339,6 +362,22 @@ gbconv_status_t launch_transpose_filter(const Dims &d, const void *w, void *wt, 
     return cuda_status(launch_pdl(transpose_krsc<__nv_bfloat16>, dim3(g), dim3(256), 0, st,
                                   (const __nv_bfloat16 *)w, (__nv_bfloat16 *)wt, d.K, d.R * d.S,
                                   d.C));
+}
+
+gbconv_status_t launch_transpose_b(const void *in, void *out, long long B, int R, int Cn,
+                                   int elem_bytes, cudaStream_t st) {
+    if (B == 0 || R == 0 || Cn == 0) return GBCONV_OK;
+    if (B > 65535 || (R + 31) / 32 > 65535) return GBCONV_ERR_UNSUPPORTED;
+    const dim3 grid((unsigned)((Cn + 31) / 32), (unsigned)((R + 31) / 32), (unsigned)B);
+    const dim3 block(32, 8);
+    cudaError_t e;
+    if (elem_bytes == 2)
+        e = launch_pdl(transpose_b<uint16_t>, grid, block, 0, st, (const uint16_t *)in,
+                       (uint16_t *)out, R, Cn);
+    else
+        e = launch_pdl(transpose_b<uint32_t>, grid, block, 0, st, (const uint32_t *)in,
+                       (uint32_t *)out, R, Cn);
+    return cuda_status(e);
 }
 
 gbconv_status_t launch_bn_fold(int K, const float *gamma, const float *bn_beta, const float *mean,

@@ -42,7 +42,7 @@ struct Fused {
 };
 
 // Error codes written to the device error word.
-enum : unsigned { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1 };
+enum : unsigned { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_BAD_INDEX = 2 };
 
 // api.cu
 Guard make_guard();                   // current device's error word + limits
@@ -53,6 +53,14 @@ gbconv_status_t cuda_status(cudaError_t e);
 // Forward with d.G >= 1 channel groups (one grid layer per group).
 gbconv_status_t launch_simt_fwd(const Dims &d, const void *x, const void *w, const float *bias,
                                 void *y, cudaStream_t st, const Fused &fz = Fused{});
+// nll.cu: negative log-likelihood loss (fp32 log-probabilities [N][C]).
+size_t nll_workspace_bytes(long long N);
+gbconv_status_t launch_nll_fwd(const float *logp, const int64_t *target, const float *weight,
+                               long long N, long long C, long long ignore_index, int reduction,
+                               float *out, float *total_weight, float *ws, cudaStream_t st);
+gbconv_status_t launch_nll_grad(const float *grad_out, const int64_t *target, const float *weight,
+                                long long N, long long C, long long ignore_index, int reduction,
+                                const float *total_weight, float *grad_in, cudaStream_t st);
 // depthwise.cu: NHWC depthwise forward (G = C = K), 8 channels per thread.
 bool depthwise_supported(const Dims &d);
 gbconv_status_t launch_depthwise(const Dims &d, const void *x, const void *w, const float *bias,
@@ -71,6 +79,9 @@ gbconv_status_t launch_bias_grad(const Dims &d, const void *g, float *db, float 
 gbconv_status_t launch_rotate_filter(const Dims &d, const void *w, void *w_rot, cudaStream_t st);
 // w[k][r][s][c] -> wT[c][r][s][k] (BF16)
 gbconv_status_t launch_transpose_filter(const Dims &d, const void *w, void *wt, cudaStream_t st);
+// out[b][j][i] = in[b][i][j], in = [B][R][Cn], 2- or 4-byte elements
+gbconv_status_t launch_transpose_b(const void *in, void *out, long long B, int R, int Cn,
+                                   int elem_bytes, cudaStream_t st);
 // scale = gamma / sqrt(var + eps), shift = bn_beta + (bias - mean) * scale
 gbconv_status_t launch_bn_fold(int K, const float *gamma, const float *bn_beta, const float *mean,
                                const float *var, float eps, const float *bias, float *scale,

@@ -61,10 +61,11 @@ def conv2d(x, w, bias=None, stride=1, padding=0, dilation=1, relu=False, layout=
                         groups)
     if out is None:
         out = torch.empty(out_shape(prob, layout), dtype=_TORCH[prob.out_dtype], device=x.device)
+    ws, nbytes = workspace(B.GBCONV_OP_FWD, prob, x.device)
     s = B.conv2d_fwd(prob, x.data_ptr(), w.data_ptr(), bias.data_ptr() if bias is not None else 0,
                      x_scale.data_ptr() if x_scale is not None else 0,
-                     w_scale.data_ptr() if w_scale is not None else 0, out.data_ptr(), 0, 0,
-                     _stream())
+                     w_scale.data_ptr() if w_scale is not None else 0, out.data_ptr(),
+                     ws.data_ptr() if nbytes else 0, nbytes, _stream())
     B.check(s, "conv2d_fwd")
     return out
 
@@ -81,8 +82,10 @@ def conv2d_fused(x, w, bias=None, scale=None, residual=None, stride=1, padding=0
     if out is None:
         out = torch.empty(out_shape(prob, layout), dtype=_TORCH[prob.out_dtype], device=x.device)
     ptr = lambda t: t.data_ptr() if t is not None else 0
+    ws, nbytes = workspace(B.GBCONV_OP_FWD, prob, x.device)
     s = B.conv2d_fwd_fused(prob, x.data_ptr(), w.data_ptr(), ptr(bias), ptr(scale), ptr(residual),
-                           ptr(x_scale), ptr(w_scale), out.data_ptr(), 0, 0, _stream())
+                           ptr(x_scale), ptr(w_scale), out.data_ptr(),
+                           ws.data_ptr() if nbytes else 0, nbytes, _stream())
     B.check(s, "conv2d_fwd_fused")
     return out
 
@@ -99,6 +102,41 @@ def bn_fold(gamma, bn_beta, mean, var, eps, bias=None):
                          shift.data_ptr(), _stream())
     B.check(s, "gbconv_bn_fold")
     return scale, shift
+
+
+_NLL_RED = {"none": 0, "mean": 1, "sum": 2}
+
+
+def nll_loss(logp, target, weight=None, ignore_index=-100, reduction="mean"):
+    """Negative log-likelihood loss forward through gbconv_nll_loss_fwd.
+    Returns (out, total_weight) as device tensors."""
+    _check_dev(logp, target, weight)
+    N, C = logp.shape
+    red = _NLL_RED[reduction]
+    out = torch.empty(N if red == 0 else 1, dtype=torch.float32, device=logp.device)
+    tw = torch.empty(1, dtype=torch.float32, device=logp.device)
+    s, nbytes = B.gbconv_nll_workspace_size(N)
+    B.check(s, "gbconv_nll_workspace_size")
+    ws = torch.empty(max(nbytes, 4), dtype=torch.uint8, device=logp.device)
+    s = B.gbconv_nll_loss_fwd(logp.data_ptr(), target.data_ptr(),
+                              weight.data_ptr() if weight is not None else 0, N, C, ignore_index,
+                              red, out.data_ptr(), tw.data_ptr(), ws.data_ptr(), nbytes, _stream())
+    B.check(s, "gbconv_nll_loss_fwd")
+    return (out if red == 0 else out[0]), tw
+
+
+def nll_loss_backward(grad_out, target, total_weight, C, weight=None, ignore_index=-100,
+                      reduction="mean"):
+    """Gradient of the loss with respect to logp through gbconv_nll_loss_bwd."""
+    _check_dev(grad_out, target, total_weight, weight)
+    N = target.numel()
+    gi = torch.empty(N, C, dtype=torch.float32, device=target.device)
+    s = B.gbconv_nll_loss_bwd(grad_out.data_ptr(), target.data_ptr(),
+                              weight.data_ptr() if weight is not None else 0, N, C, ignore_index,
+                              _NLL_RED[reduction], total_weight.data_ptr(), gi.data_ptr(),
+                              _stream())
+    B.check(s, "gbconv_nll_loss_bwd")
+    return gi
 
 
 def workspace(op, prob, device):

@@ -112,9 +112,12 @@ def test_tensor_core_alignment_rules():
 
 
 def test_unsupported_combinations():
-    # BF16 NCHW and F32 -> BF16 are not offered
+    # BF16 NCHW forward needs its layout-transform workspace; its gradients and
+    # F32 -> BF16 are not offered
     p = B.problem(2, 16, 8, 8, 8, 3, 3, 1, 1, 1, B.GBCONV_BF16, B.GBCONV_BF16, B.GBCONV_NCHW)
-    assert B.conv2d_fwd(p, 4096, 8192, 0, 0, 0, 12288, 0, 0, 0) == B.GBCONV_ERR_UNSUPPORTED
+    assert B.conv2d_fwd(p, 4096, 8192, 0, 0, 0, 12288, 0, 0, 0) == B.GBCONV_ERR_WORKSPACE
+    s, n = B.gbconv_workspace_size(B.GBCONV_OP_FWD, p)
+    assert s == B.GBCONV_OK and n == 4096 + 2304 + 2048  # x, w, y, each rounded to 256 B
     p = B.problem(2, 16, 8, 8, 8, 3, 3, 1, 1, 1, B.GBCONV_F32, B.GBCONV_BF16)
     assert B.conv2d_fwd(p, 4096, 8192, 0, 0, 0, 12288, 0, 0, 0) == B.GBCONV_ERR_UNSUPPORTED
     # E4M3 output is never produced
