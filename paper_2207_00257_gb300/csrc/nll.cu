@@ -13,9 +13,9 @@
 // reduces the partials in the same fixed tree order. A target outside
 // [0, C) that is not ignore_index sets DEVERR_BAD_INDEX in the device error
 // word and counts as ignored.
-// Gradient: one write per element of [N][C]: -w_n * g at (n, target[n]) of
-// counted rows (g = grad_out[n], grad_out[0], or grad_out[0] / total_weight),
-// zero elsewhere.
+// Gradient: one write per element of [N][C], a warp per row: -w_n * g at
+// (n, target[n]) of counted rows (g = grad_out[n], grad_out[0], or
+// grad_out[0] / total_weight), zero elsewhere.
 #include <cstdint>
 
 #include "internal.h"
@@ -100,27 +100,49 @@ __global__ void __launch_bounds__(NLL_THREADS) nll_final(const float *__restrict
     }
 }
 
+// One row per warp-iteration: the row's zeros (16-byte stores when C % 4 == 0
+// and grad_in is 16-byte aligned) with -w_n * g at column target[n].
 __global__ void nll_grad(const float *__restrict__ grad_out, const int64_t *__restrict__ target,
                          const float *__restrict__ weight, long long N, long long C,
                          long long ignore_index, int reduction,
-                         const float *__restrict__ total_weight, float *grad_in, unsigned *err) {
+                         const float *__restrict__ total_weight, float *grad_in, int vec4,
+                         unsigned *err) {
     ptx::griddep_wait();
     if (threadIdx.x == 0) ptx::griddep_launch();
-    const long long total = N * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long n = i / C, c = i - n * C;
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long n = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); n < N;
+         n += warps) {
         const long long t = target[n];
+        long long tc = -1;  // column of the row's only non-zero
         float v = 0.f;
-        if (t == c && t != ignore_index) {
-            const float w = weight ? weight[t] : 1.f;
-            const float g = reduction == 0 ? grad_out[n]
-                            : reduction == 1 ? grad_out[0] / total_weight[0] : grad_out[0];
-            v = -w * g;
-        } else if (c == 0 && t != ignore_index && (t < 0 || t >= C)) {
-            atomicOr(err, DEVERR_BAD_INDEX);
+        if (t != ignore_index) {
+            if (t < 0 || t >= C) {
+                if (lane == 0) atomicOr(err, DEVERR_BAD_INDEX);
+            } else {
+                const float w = weight ? weight[t] : 1.f;
+                const float g = reduction == 0 ? grad_out[n]
+                                : reduction == 1 ? grad_out[0] / total_weight[0] : grad_out[0];
+                v = -w * g;
+                tc = t;
+            }
         }
-        grad_in[i] = v;
+        float *row = grad_in + n * C;
+        if (vec4) {
+            for (long long c = 4 * lane; c < C; c += 128) {
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (tc >= c && tc < c + 4) {
+                    const int k = (int)(tc - c);
+                    q.x = k == 0 ? v : 0.f;
+                    q.y = k == 1 ? v : 0.f;
+                    q.z = k == 2 ? v : 0.f;
+                    q.w = k == 3 ? v : 0.f;
+                }
+                *reinterpret_cast<float4 *>(row + c) = q;
+            }
+        } else {
+            for (long long c = lane; c < C; c += 32) row[c] = c == tc ? v : 0.f;
+        }
     }
 }
 
@@ -151,12 +173,13 @@ gbconv_status_t launch_nll_grad(const float *grad_out, const int64_t *target, co
                                 const float *total_weight, float *grad_in, cudaStream_t st) {
     const Guard g = make_guard();
     if (!g.err) return GBCONV_ERR_CUDA;
-    const long long total = N * C;
-    if (total == 0) return GBCONV_OK;
-    const long long blocks = (total + 255) / 256;
-    const unsigned grid = (unsigned)(blocks < (long long)sm_count() * 8 ? blocks : sm_count() * 8);
+    if (N * C == 0) return GBCONV_OK;
+    const int vec4 = C % 4 == 0 && reinterpret_cast<uintptr_t>(grad_in) % 16 == 0;
+    const long long blocks = (N + 7) / 8;  // 8 rows (warps) per block
+    const unsigned grid = (unsigned)(blocks < (long long)sm_count() * 16 ? blocks : sm_count() * 16);
     return cuda_status(launch_pdl(nll_grad, dim3(grid), dim3(256), 0, st, grad_out, target, weight,
-                                  N, C, ignore_index, reduction, total_weight, grad_in, g.err));
+                                  N, C, ignore_index, reduction, total_weight, grad_in, vec4,
+                                  g.err));
 }
 
 }  // namespace gbc
