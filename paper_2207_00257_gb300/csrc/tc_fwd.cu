@@ -176,6 +176,34 @@ __global__ void __launch_bounds__(EpiShape<BN>::threads, 1) tc_fwd_kernel(const 
             ptx::prefetch_tmap(&prm.tmB[g]);
             ptx::prefetch_tmap(&prm.tmY[g]);
         }
+    // The first tile's operand boxes into L2 while the previous kernel
+    // drains. A prefetch moves nothing into shared memory or registers, and L2
+    // stays coherent with the previous kernel's writes, so it is safe before
+    // the dependency wait; the loads themselves come after it.
+    if (threadIdx.x == 0 && (int)blockIdx.x < prm.num_tiles) {
+        int g, mt, nt;
+        decode(prm, blockIdx.x, g, mt, nt);
+        const ProbArgs &pa = prm.pa[g];
+        const int m0 = mt * BM;
+        const int q = m0 % pa.Q, t = m0 / pa.Q;
+        const int p = t % pa.P, n = t / pa.P;
+        const int wc = q * pa.v - pa.pw, hc = p * pa.u - pa.ph;
+        int r = 0, s = 0;
+        for (int rs = 0; rs < pa.RS; ++rs) {
+            for (int cb = 0; cb < pa.c_blocks; ++cb) {
+                if (pa.a_tiled)
+                    ptx::tma_prefetch_2d(&prm.tmA[g], cb * KE, m0);
+                else
+                    ptx::tma_prefetch_im2col_4d(&prm.tmA[g], cb * KE, wc, hc, n,
+                                                (uint16_t)(s * pa.dw), (uint16_t)(r * pa.dh));
+                ptx::tma_prefetch_3d(&prm.tmB[g], cb * KE, rs, nt * pa.bn);
+            }
+            if (++s == pa.S) {
+                s = 0;
+                ++r;
+            }
+        }
+    }
     // Prologue done: now wait for the kernels this one depends on, and let the
     // next kernel on the stream start launching.
     ptx::griddep_wait();

@@ -227,6 +227,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
     if (threadIdx.x == 0) {  // descriptors do not depend on earlier kernels
         ptx::prefetch_tmap(&prm.tmX);
         ptx::prefetch_tmap(&prm.tmW);
+        // The first tile's bands and filter tiles into L2 while the previous
+        // kernel drains (a prefetch fills only L2, which stays coherent with
+        // that kernel's writes; the loads come after the dependency wait).
+        if ((int)blockIdx.x < prm.num_tiles) {
+            const Tile T = tdecode<OPH>(prm, blockIdx.x);
+            for (int cb = 0; cb < prm.c_blocks; ++cb)
+                for (int f = T.f0; f < T.f1; ++f) {
+                    if (prm.flat)
+                        ptx::tma_prefetch_2d(&prm.tmX, cb * KE, T.p0);
+                    else
+                        ptx::tma_prefetch_4d(&prm.tmX, cb * KE, prm.ph_w0[f],
+                                             prm.u * T.p0 + prm.ph_h0[f], T.n);
+                    for (int ti = f ? prm.ph_end[f - 1] : 0; ti < prm.ph_end[f]; ++ti)
+                        ptx::tma_prefetch_3d(&prm.tmW, cb * KE, prm.tap_t[ti],
+                                             prm.w_resident ? 0 : T.kt * KT);
+                }
+        }
     }
     ptx::griddep_wait();
     if (threadIdx.x == 0) ptx::griddep_launch();
