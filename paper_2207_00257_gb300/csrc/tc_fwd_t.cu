@@ -838,7 +838,8 @@ gbconv_status_t launch(const TParams &prm, size_t smem, int grid, cudaStream_t s
 // Output-channel tile of the transposed kernel for this layer (0 if none fits).
 int tc_fwd_t_tile(const Dims &d) {
     if (!tc_fwd_supported(d)) return 0;
-    if (d.K > 128 && !is_flat(d)) return 0;  // a band would be fetched once per channel tile
+    // K > 128: a band is fetched once per 128-channel tile (automatic choice
+    // only when the filter could not stay resident in the pixel-major band kernel)
     const int kt = d.K <= 64 ? 64 : 128;
     TPlan p;
     return make_plan(d, kt, &p) ? kt : 0;
