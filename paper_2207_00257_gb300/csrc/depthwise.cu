@@ -86,6 +86,20 @@ __device__ __forceinline__ void unpack8(const uint4 &u, float (&v)[8]) {
     }
 }
 
+// One tap's 8 x CG staged weights (32-byte aligned) as 16-byte shared loads:
+// scalar loads at a 32-byte lane stride would conflict eight ways.
+template <int CG>
+__device__ __forceinline__ void load_taps(const float *wp, float (&wv)[8 * CG]) {
+#pragma unroll
+    for (int i = 0; i < 2 * CG; ++i) {
+        const float4 q = reinterpret_cast<const float4 *>(wp)[i];
+        wv[4 * i] = q.x;
+        wv[4 * i + 1] = q.y;
+        wv[4 * i + 2] = q.z;
+        wv[4 * i + 3] = q.w;
+    }
+}
+
 // SC > 0 (BF16 input only): the filter width is the constant SC, so each
 // filter row's SC x PX vector loads are unrolled and issued together.
 template <typename Ti, typename To, int CG, int SC>
@@ -137,7 +151,8 @@ __global__ void __launch_bounds__(DW_THREADS, Px<CG>::min_blocks) depthwise_kern
                     }
 #pragma unroll
                 for (int s = 0; s < SC; ++s) {
-                    const float *wp = wsm + ((r * SC + s) * C + c0) * CG;
+                    float wv[8 * CG];
+                    load_taps<CG>(wsm + ((r * SC + s) * C + c0) * CG, wv);
 #pragma unroll
                     for (int a = 0; a < PX; ++a) {
                         float xv[8];
@@ -147,19 +162,15 @@ __global__ void __launch_bounds__(DW_THREADS, Px<CG>::min_blocks) depthwise_kern
                             const int gb = (j / CG) * CG;
 #pragma unroll
                             for (int c = 0; c < CG; ++c)
-                                acc[a][j] = fmaf(xv[gb + c], wp[j * CG + c], acc[a][j]);
+                                acc[a][j] = fmaf(xv[gb + c], wv[j * CG + c], acc[a][j]);
                         }
                     }
                 }
                 continue;
             }
             for (int s = 0; s < prm.S; ++s) {
-                float wv[8][CG];  // this tap's weights of the thread's 8 output channels
-                const float *wp = wsm + ((r * prm.S + s) * C + c0) * CG;
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-#pragma unroll
-                    for (int c = 0; c < CG; ++c) wv[j][c] = wp[j * CG + c];
+                float wv[8 * CG];  // this tap's weights of the thread's 8 output channels
+                load_taps<CG>(wsm + ((r * prm.S + s) * C + c0) * CG, wv);
 #pragma unroll
                 for (int a = 0; a < PX; ++a) {
                     const int ww = (q0 + a) * prm.v + s * prm.dw - prm.pw;
@@ -170,7 +181,7 @@ __global__ void __launch_bounds__(DW_THREADS, Px<CG>::min_blocks) depthwise_kern
                     for (int j = 0; j < 8; ++j) {
                         const int gb = (j / CG) * CG;  // first channel of j's group in the vector
 #pragma unroll
-                        for (int c = 0; c < CG; ++c) acc[a][j] = fmaf(xv[gb + c], wv[j][c], acc[a][j]);
+                        for (int c = 0; c < CG; ++c) acc[a][j] = fmaf(xv[gb + c], wv[j * CG + c], acc[a][j]);
                     }
                 }
             }
