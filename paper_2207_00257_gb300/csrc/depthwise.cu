@@ -66,10 +66,11 @@ __device__ __forceinline__ void store8(__nv_bfloat16 *p, const float (&v)[8]) {
     *reinterpret_cast<uint4 *>(p) = u;
 }
 
-// Output pixels per thread (consecutive q), sharing each filter load.
+// Output pixels per thread (consecutive q), sharing each filter load (two for
+// 8-channel groups, whose 64 weights per tap already fill the registers).
 template <int CG>
 struct Px {
-    static constexpr int v = 4;
+    static constexpr int v = CG == 8 ? 2 : 4;
     static constexpr int min_blocks = 2;
 };
 
@@ -169,19 +170,28 @@ __global__ void __launch_bounds__(DW_THREADS, Px<CG>::min_blocks) depthwise_kern
                 continue;
             }
             for (int s = 0; s < prm.S; ++s) {
+                // this tap's PX input vectors first (all loads in flight), then the math
+                float xv[PX][8];
+#pragma unroll
+                for (int a = 0; a < PX; ++a) {
+                    const int ww = (q0 + a) * prm.v + s * prm.dw - prm.pw;
+                    if (q0 + a < prm.Q && ww >= 0 && ww < prm.W) {
+                        load8(xrow + (long long)ww * C, xv[a]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) xv[a][j] = 0.f;
+                    }
+                }
                 float wv[8 * CG];  // this tap's weights of the thread's 8 output channels
                 load_taps<CG>(wsm + ((r * prm.S + s) * C + c0) * CG, wv);
 #pragma unroll
                 for (int a = 0; a < PX; ++a) {
-                    const int ww = (q0 + a) * prm.v + s * prm.dw - prm.pw;
-                    if (q0 + a >= prm.Q || ww < 0 || ww >= prm.W) continue;
-                    float xv[8];
-                    load8(xrow + (long long)ww * C, xv);
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int gb = (j / CG) * CG;  // first channel of j's group in the vector
 #pragma unroll
-                        for (int c = 0; c < CG; ++c) acc[a][j] = fmaf(xv[gb + c], wv[j * CG + c], acc[a][j]);
+                        for (int c = 0; c < CG; ++c)
+                            acc[a][j] = fmaf(xv[a][gb + c], wv[j * CG + c], acc[a][j]);
                     }
                 }
             }
@@ -229,9 +239,12 @@ template <typename Ti, typename To>
 gbconv_status_t launch_cg(const Dims &d, const void *x, const void *w, void *y, size_t smem,
                           const DwParams &prm, cudaStream_t st) {
     if constexpr (std::is_same<Ti, __nv_bfloat16>::value) {
-        // unrolled rows where their registers fit: 1 or 2 channels per group
+        // unrolled rows where their registers fit: 1 or 2 channels per group, 4 for BF16 output
         if (d.S == 3 && d.C == d.G) return launch_typed<Ti, To, 1, 3>(d, x, w, y, smem, prm, st);
         if (d.S == 3 && d.C == 2 * d.G) return launch_typed<Ti, To, 2, 3>(d, x, w, y, smem, prm, st);
+        if constexpr (std::is_same<To, __nv_bfloat16>::value) {
+            if (d.S == 3 && d.C == 4 * d.G) return launch_typed<Ti, To, 4, 3>(d, x, w, y, smem, prm, st);
+        }
     }
     switch (d.C / d.G) {
         case 1: return launch_typed<Ti, To, 1, 0>(d, x, w, y, smem, prm, st);
