@@ -14,7 +14,9 @@
 // pixels of one row, reads x as 16-byte (BF16) or 32-byte (FP32) channel
 // vectors per tap (a warp covers 32 x 8 consecutive channels, so its loads and
 // stores are contiguous) and accumulates in FP32 in the order r, s, c. The
-// filter is staged once per block in shared memory as FP32 [R*S][K][CG].
+// filter is staged once per block in shared memory as FP32, laid out so that
+// neighbouring lanes (neighbouring channel vectors) read neighbouring 16-byte
+// words: [R*S][2*CG float4 slots][K/8 channel vectors].
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -87,13 +89,15 @@ __device__ __forceinline__ void unpack8(const uint4 &u, float (&v)[8]) {
     }
 }
 
-// One tap's 8 x CG staged weights (32-byte aligned) as 16-byte shared loads:
-// scalar loads at a 32-byte lane stride would conflict eight ways.
+// One tap's 8 x CG weights of channel vector cvi as 2*CG 16-byte shared
+// loads, slot-major: a warp's lanes read consecutive words of one slot, with
+// no bank conflict for any CG. Weight f of the vector (f = j*CG + c for
+// output channel c0 + j and group channel c) is word f%4 of slot f/4.
 template <int CG>
-__device__ __forceinline__ void load_taps(const float *wp, float (&wv)[8 * CG]) {
+__device__ __forceinline__ void load_taps(const float4 *wp, int cv, float (&wv)[8 * CG]) {
 #pragma unroll
     for (int i = 0; i < 2 * CG; ++i) {
-        const float4 q = reinterpret_cast<const float4 *>(wp)[i];
+        const float4 q = wp[i * cv];
         wv[4 * i] = q.x;
         wv[4 * i + 1] = q.y;
         wv[4 * i + 2] = q.z;
@@ -102,34 +106,42 @@ __device__ __forceinline__ void load_taps(const float *wp, float (&wv)[8 * CG]) 
 }
 
 // SC > 0 (BF16 input only): the filter width is the constant SC, so each
-// filter row's SC x PX vector loads are unrolled and issued together.
-template <typename Ti, typename To, int CG, int SC>
+// filter row's SC x PX vector loads are unrolled and issued together. UNIT
+// (horizontal stride and dilation 1): the PX pixels' SC taps cover only
+// PX + SC - 1 input columns, each loaded (and, up to two channels per group,
+// converted to FP32) once per filter row. Work items are numbered in 32 bits
+// (fewer than 2^31, checked on the host).
+template <typename Ti, typename To, int CG, int SC, bool UNIT>
 __global__ void __launch_bounds__(DW_THREADS, Px<CG>::min_blocks) depthwise_kernel(
     const Ti *__restrict__ x, const Ti *__restrict__ w, To *y, const DwParams prm) {
     constexpr int PX = Px<CG>::v;
-    extern __shared__ float4 wsm4[];
-    float *wsm = reinterpret_cast<float *>(wsm4);  // [R*S][K][CG]
-    const int RS = prm.R * prm.S, C = prm.C;       // C = K
+    extern __shared__ float4 wsm4[];  // [R*S][2*CG][C/8]
+    float *wsm = reinterpret_cast<float *>(wsm4);
+    const int RS = prm.R * prm.S, C = prm.C;  // C = K
+    const int cv = C / 8;                     // channel vectors per pixel
     // The filter is a kernel input like x: read it after the dependency wait.
     ptx::griddep_wait();
     for (int i = threadIdx.x; i < RS * C * CG; i += blockDim.x) {
-        const int c = i % CG, t = i / CG, k = t % C, rs = t / C;
+        const int e = i & 3;
+        int t = i >> 2;
+        const int cvi = t % cv;
+        t /= cv;
+        const int f = (t % (2 * CG)) * 4 + e, rs = t / (2 * CG);
+        const int k = cvi * 8 + f / CG, c = f % CG;
         wsm[i] = static_cast<float>(w[((long long)k * RS + rs) * CG + c]);
     }
     __syncthreads();
     if (threadIdx.x == 0) ptx::griddep_launch();
-    const int cv = C / 8;                    // channel vectors per pixel
-    const int qb = (prm.Q + PX - 1) / PX;    // pixel blocks per output row
-    const long long total = (long long)prm.N * prm.P * qb * cv;
+    const unsigned qb = (prm.Q + PX - 1) / PX;  // pixel blocks per output row
+    const unsigned total = (unsigned)prm.N * prm.P * qb * cv;
     const To *z = static_cast<const To *>(prm.z);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int c0 = (int)(i % cv) * 8;
-        long long t = i / cv;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int c0 = (int)(i % (unsigned)cv) * 8;
+        unsigned t = i / (unsigned)cv;
         const int q0 = (int)(t % qb) * PX;
         t /= qb;
-        const int p = (int)(t % prm.P);
-        const int n = (int)(t / prm.P);
+        const int p = (int)(t % (unsigned)prm.P);
+        const int n = (int)(t / (unsigned)prm.P);
         float acc[PX][8];
 #pragma unroll
         for (int a = 0; a < PX; ++a)
@@ -139,7 +151,53 @@ __global__ void __launch_bounds__(DW_THREADS, Px<CG>::min_blocks) depthwise_kern
             const int h = p * prm.u + r * prm.dh - prm.ph;
             if (h < 0 || h >= prm.H) continue;
             const Ti *xrow = x + ((long long)n * prm.H + h) * prm.W * C + c0;
-            if constexpr (SC > 0) {
+            if constexpr (SC > 0 && UNIT) {
+                constexpr int NX = PX + SC - 1;
+                uint4 xr[NX];
+#pragma unroll
+                for (int e = 0; e < NX; ++e) {
+                    const int ww = q0 + e - prm.pw;
+                    xr[e] = (ww >= 0 && ww < prm.W) ? ldraw(xrow + ww * C) : make_uint4(0, 0, 0, 0);
+                }
+                if constexpr (CG <= 2) {
+                    float xv[NX][8];
+#pragma unroll
+                    for (int e = 0; e < NX; ++e) unpack8(xr[e], xv[e]);
+#pragma unroll
+                    for (int s = 0; s < SC; ++s) {
+                        float wv[8 * CG];
+                        load_taps<CG>(wsm4 + (r * SC + s) * 2 * CG * cv + c0 / 8, cv, wv);
+#pragma unroll
+                        for (int a = 0; a < PX; ++a)
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int gb = (j / CG) * CG;
+#pragma unroll
+                                for (int c = 0; c < CG; ++c)
+                                    acc[a][j] = fmaf(xv[a + s][gb + c], wv[j * CG + c], acc[a][j]);
+                            }
+                    }
+                } else {
+#pragma unroll
+                    for (int s = 0; s < SC; ++s) {
+                        float wv[8 * CG];
+                        load_taps<CG>(wsm4 + (r * SC + s) * 2 * CG * cv + c0 / 8, cv, wv);
+#pragma unroll
+                        for (int a = 0; a < PX; ++a) {
+                            float xv[8];
+                            unpack8(xr[a + s], xv);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int gb = (j / CG) * CG;
+#pragma unroll
+                                for (int c = 0; c < CG; ++c)
+                                    acc[a][j] = fmaf(xv[gb + c], wv[j * CG + c], acc[a][j]);
+                            }
+                        }
+                    }
+                }
+                continue;
+            } else if constexpr (SC > 0) {
                 uint4 xr[SC][PX];
 #pragma unroll
                 for (int s = 0; s < SC; ++s)
@@ -153,7 +211,7 @@ __global__ void __launch_bounds__(DW_THREADS, Px<CG>::min_blocks) depthwise_kern
 #pragma unroll
                 for (int s = 0; s < SC; ++s) {
                     float wv[8 * CG];
-                    load_taps<CG>(wsm + ((r * SC + s) * C + c0) * CG, wv);
+                    load_taps<CG>(wsm4 + (r * SC + s) * 2 * CG * cv + c0 / 8, cv, wv);
 #pragma unroll
                     for (int a = 0; a < PX; ++a) {
                         float xv[8];
@@ -183,7 +241,7 @@ __global__ void __launch_bounds__(DW_THREADS, Px<CG>::min_blocks) depthwise_kern
                     }
                 }
                 float wv[8 * CG];  // this tap's weights of the thread's 8 output channels
-                load_taps<CG>(wsm + ((r * prm.S + s) * C + c0) * CG, wv);
+                load_taps<CG>(wsm4 + (r * prm.S + s) * 2 * CG * cv + c0 / 8, cv, wv);
 #pragma unroll
                 for (int a = 0; a < PX; ++a) {
 #pragma unroll
@@ -216,13 +274,13 @@ __global__ void __launch_bounds__(DW_THREADS, Px<CG>::min_blocks) depthwise_kern
     }
 }
 
-template <typename Ti, typename To, int CG, int SC>
+template <typename Ti, typename To, int CG, int SC, bool UNIT = false>
 gbconv_status_t launch_typed(const Dims &d, const void *x, const void *w, void *y, size_t smem,
                              const DwParams &prm, cudaStream_t st) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(depthwise_kernel<Ti, To, CG, SC>,
+        attr_err = cudaFuncSetAttribute(depthwise_kernel<Ti, To, CG, SC, UNIT>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, DW_SMEM_LIMIT);
     });
     if (attr_err != cudaSuccess) return cuda_status(attr_err);
@@ -230,7 +288,7 @@ gbconv_status_t launch_typed(const Dims &d, const void *x, const void *w, void *
     const long long total = (long long)d.N * d.P * ((d.Q + PX - 1) / PX) * (d.C / 8);
     const long long blocks = (total + DW_THREADS - 1) / DW_THREADS;
     const unsigned grid = (unsigned)std::min<long long>(blocks, (long long)sm_count() * 8);
-    return cuda_status(launch_pdl(depthwise_kernel<Ti, To, CG, SC>, dim3(grid), dim3(DW_THREADS), smem,
+    return cuda_status(launch_pdl(depthwise_kernel<Ti, To, CG, SC, UNIT>, dim3(grid), dim3(DW_THREADS), smem,
                                   st, static_cast<const Ti *>(x), static_cast<const Ti *>(w),
                                   static_cast<To *>(y), prm));
 }
@@ -240,10 +298,17 @@ gbconv_status_t launch_cg(const Dims &d, const void *x, const void *w, void *y, 
                           const DwParams &prm, cudaStream_t st) {
     if constexpr (std::is_same<Ti, __nv_bfloat16>::value) {
         // unrolled rows where their registers fit: 1 or 2 channels per group, 4 for BF16 output
-        if (d.S == 3 && d.C == d.G) return launch_typed<Ti, To, 1, 3>(d, x, w, y, smem, prm, st);
-        if (d.S == 3 && d.C == 2 * d.G) return launch_typed<Ti, To, 2, 3>(d, x, w, y, smem, prm, st);
+        const bool unit = d.v == 1 && d.dw == 1;
+        if (d.S == 3 && d.C == d.G)
+            return unit ? launch_typed<Ti, To, 1, 3, true>(d, x, w, y, smem, prm, st)
+                        : launch_typed<Ti, To, 1, 3>(d, x, w, y, smem, prm, st);
+        if (d.S == 3 && d.C == 2 * d.G)
+            return unit ? launch_typed<Ti, To, 2, 3, true>(d, x, w, y, smem, prm, st)
+                        : launch_typed<Ti, To, 2, 3>(d, x, w, y, smem, prm, st);
         if constexpr (std::is_same<To, __nv_bfloat16>::value) {
-            if (d.S == 3 && d.C == 4 * d.G) return launch_typed<Ti, To, 4, 3>(d, x, w, y, smem, prm, st);
+            if (d.S == 3 && d.C == 4 * d.G)
+                return unit ? launch_typed<Ti, To, 4, 3, true>(d, x, w, y, smem, prm, st)
+                            : launch_typed<Ti, To, 4, 3>(d, x, w, y, smem, prm, st);
         }
     }
     switch (d.C / d.G) {
@@ -263,6 +328,8 @@ bool depthwise_supported(const Dims &d) {
     if (!((d.in_dtype == GBCONV_F32 && d.out_dtype == GBCONV_F32) ||
           (d.in_dtype == GBCONV_BF16 && (d.out_dtype == GBCONV_BF16 || d.out_dtype == GBCONV_F32))))
         return false;
+    // work items (at least two pixels each) are numbered in 32 bits
+    if ((long long)d.N * d.P * ((d.Q + 1) / 2) * (d.C / 8) >= (1LL << 31)) return false;
     return (long long)d.R * d.S * d.C * cg * 4 <= DW_SMEM_LIMIT;
 }
 

@@ -57,6 +57,9 @@ SMALL_GROUPS = [  # C/G = K/G in {2, 4, 8}: the direct kernel of the depthwise c
     (2, 128, 8, 8, 128, 3, 3, 1, 1, 1, 32),     # 4 channels per group (ResNeXt-style)
     (1, 64, 9, 10, 64, 3, 3, 2, 1, 1, 32),      # 2 channels per group, stride 2
     (2, 64, 7, 9, 64, 5, 3, 1, (2, 1), 1, 8),   # 8 channels per group
+    (2, 64, 9, 13, 64, 3, 3, 1, 1, 1, 32),      # 2 channels per group, unit stride
+    (1, 32, 7, 10, 32, 3, 3, 1, (1, 2), 1, 16), # unit stride, horizontal padding 2
+    (2, 128, 9, 11, 128, 3, 3, 2, 1, 1, 32),    # 4 channels per group, stride 2
 ]
 CUDA_CORE_GROUPS = [
     (2, 32, 9, 9, 64, 3, 3, 1, 1, 1, 32),       # depthwise with multiplier 2
