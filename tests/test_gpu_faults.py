@@ -1,7 +1,8 @@
 """Failure detection without a GPU fault: the test control
-GBCONV_DEBUG_SKIP_LOADS makes the tensor-core producer issue no loads, so the
-consumers' bounded waits run out; the kernel must record a timeout, free its
-Tensor Memory and return, and the context must stay usable."""
+GBCONV_DEBUG_SKIP_LOADS makes the tensor-core producer (and the staged
+depthwise kernel's copy issuer) issue no loads, so the consumers' bounded
+waits run out; the kernel must record a timeout, free its Tensor Memory and
+return, and the context must stay usable."""
 import pytest
 import torch
 
@@ -35,5 +36,28 @@ def test_wait_timeout_reported_and_context_survives():
         B.gbconv_debug_set(B.GBCONV_DEBUG_WAIT_LIMIT_NS, 0)
     # the word was cleared and the next launch (which needs all TMEM) works
     y = F.conv2d(xb, wb, bb, 1, 1, 1, True)
+    F.device_error()
+    assert torch.equal(y, ref)
+
+
+def test_staged_depthwise_wait_timeout_reported():
+    """The staged depthwise kernel waits on its row copies with the same
+    bounded wait: no copies issued -> timeout recorded, context usable."""
+    N, C, H, W = 2, 64, 9, 9
+    g = torch.Generator().manual_seed(41)
+    xb = torch.randn(N, H, W, C, generator=g).bfloat16().cuda()
+    wb = (torch.randn(C, 3, 3, 1, generator=g) / 3).bfloat16().cuda()
+    ref = F.conv2d(xb, wb, None, 1, 1, 1, True, groups=C)
+    F.device_error()
+    B.check(B.gbconv_debug_set(B.GBCONV_DEBUG_WAIT_LIMIT_NS, 20_000_000), "debug")  # 20 ms
+    B.check(B.gbconv_debug_set(B.GBCONV_DEBUG_SKIP_LOADS, 1), "debug")
+    try:
+        F.conv2d(xb, wb, None, 1, 1, 1, True, groups=C)
+        st = B.gbconv_get_device_error(torch.cuda.current_stream().cuda_stream)
+        assert st == B.GBCONV_ERR_TIMEOUT
+    finally:
+        B.gbconv_debug_set(B.GBCONV_DEBUG_SKIP_LOADS, 0)
+        B.gbconv_debug_set(B.GBCONV_DEBUG_WAIT_LIMIT_NS, 0)
+    y = F.conv2d(xb, wb, None, 1, 1, 1, True, groups=C)
     F.device_error()
     assert torch.equal(y, ref)

@@ -9,7 +9,7 @@ import oracle
 from paper_2207_00257_gb300 import binding as B
 from paper_2207_00257_gb300 import functional as F
 
-from _gpu_helpers import TOL_ACC32, TOL_BF16_OUT, TOL_F32, f64
+from _gpu_helpers import TOL_ACC32, TOL_BF16_OUT, TOL_F32, f64, sampled
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +61,11 @@ SMALL_GROUPS = [  # C/G = K/G in {2, 4, 8}: the direct kernel of the depthwise c
     (1, 32, 7, 10, 32, 3, 3, 1, (1, 2), 1, 16), # unit stride, horizontal padding 2
     (2, 128, 9, 11, 128, 3, 3, 2, 1, 1, 32),    # 4 channels per group, stride 2
 ]
+DIRECT_BF16 = [  # rows too wide to stage two bands in shared memory: the direct kernel
+    (1, 2048, 4, 24, 2048, 3, 3, 1, 1, 1, 2048),
+    (1, 1024, 3, 40, 1024, 3, 3, 1, 1, 1, 256),  # 4 channels per group
+    (1, 1024, 5, 30, 1024, 3, 3, 2, 1, 1, 512),  # 2 channels per group, stride 2
+]
 CUDA_CORE_GROUPS = [
     (2, 32, 9, 9, 64, 3, 3, 1, 1, 1, 32),       # depthwise with multiplier 2
     (1, 12, 7, 8, 18, 3, 2, (2, 1), (1, 0), 1, 6),
@@ -100,12 +105,41 @@ def test_small_groups_direct_kernel(case, dt):
     assert err <= (TOL_BF16_OUT if outd == torch.bfloat16 else TOL_F32), err
 
 
+@pytest.mark.parametrize("case", DIRECT_BF16, ids=_cid)
+@pytest.mark.parametrize("out", ["bf16", "f32"])
+def test_groups_direct_kernel_wide_rows(case, out):
+    od = torch.bfloat16 if out == "bf16" else torch.float32
+    err = _case(*case, "NHWC", torch.bfloat16, od, seed=95, fused=True)
+    assert err <= (TOL_BF16_OUT if out == "bf16" else TOL_ACC32), err
+
+
 @pytest.mark.parametrize("case", CUDA_CORE_GROUPS + SMALL_GROUPS[:1], ids=_cid)
 @pytest.mark.parametrize("layout", ["NHWC", "NCHW"])
 def test_groups_cuda_cores(case, layout):
     ind = torch.bfloat16 if layout == "NHWC" else torch.float32
     err = _case(*case, layout, ind, torch.float32, seed=92, fused=True)
     assert err <= (TOL_ACC32 if ind == torch.bfloat16 else TOL_F32), err
+
+
+# (N, C, HW, G): the bench's grouped layers at batch 32 (two blocks per SM,
+# about six bands each), and a 256-channel depthwise layer whose two stages
+# take one block per SM; both refill stages while the other band computes.
+FULL_SIZE = [(32, 128, 56, 128), (32, 128, 56, 32), (8, 256, 56, 256)]
+
+
+@pytest.mark.parametrize("N,C,HW,G", FULL_SIZE, ids=lambda v: str(v))
+def test_groups_full_size_sampled(N, C, HW, G):
+    p = oracle.Conv(N, C, HW, HW, C, 3, 3, 1, 1, 1, "NHWC", groups=G)
+    g = torch.Generator().manual_seed(96)
+    x = torch.randn(p.x_shape, generator=g).bfloat16()
+    w = (torch.randn(p.w_shape, generator=g) / np.sqrt(C // G * 9)).bfloat16()
+    b = torch.rand(C, generator=g) * 0.2 - 0.1
+    y = F.conv2d(x.cuda(), w.cuda(), b.cuda(), 1, 1, 1, True, groups=G)
+    F.device_error()
+    idx = sampled(int(np.prod(p.y_shape)), 8000, seed=97)
+    ref, bound = oracle.conv2d_fwd(p, f64(x), f64(w), f64(b), True, idx=idx, with_bound=True)
+    err = oracle.max_normalised_error(f64(y).reshape(-1)[idx], ref.reshape(-1), bound.reshape(-1))
+    assert err <= TOL_BF16_OUT, err
 
 
 def test_groups_with_fused_epilogue_on_tensor_core_shapes():
