@@ -95,27 +95,26 @@ struct Px {
 };
 
 // Raw 16-byte channel vector of 8 BF16 values, unpacked at use: all of a
-// filter row's loads are issued before the first multiply. SMEM: the pointer
-// is into shared memory (staged rows), read with an explicit shared load.
-template <bool SMEM>
+// filter row's loads are issued before the first multiply. Global rows are
+// read through a pointer, staged rows by 32-bit shared-memory address.
 __device__ __forceinline__ uint4 ldraw(const __nv_bfloat16 *p) {
-    if constexpr (SMEM) {
-        uint4 v;
-        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                     : "r"(ptx::smem_addr(p)));
-        return v;
-    } else {
-        return *reinterpret_cast<const uint4 *>(p);
-    }
+    return *reinterpret_cast<const uint4 *>(p);
 }
+__device__ __forceinline__ uint4 ldraw_s(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(a));
+    return v;
+}
+// BF16 is the upper half of an FP32 word, so widening is exact bit
+// placement: the low element of a 32-bit pair shifted up, the high one masked.
 __device__ __forceinline__ void unpack8(const uint4 &u, float (&v)[8]) {
-    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const float2 f = __bfloat1622float2(h[i]);
-        v[2 * i] = f.x;
-        v[2 * i + 1] = f.y;
+        v[2 * i] = __uint_as_float(w[i] << 16);
+        v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
     }
 }
 
@@ -135,16 +134,37 @@ __device__ __forceinline__ void load_taps(const float4 *wp, int cv, float (&wv)[
     }
 }
 
+// (d0, d1) = (a0*b0 + d0, a1*b1 + d1), each rounded once: the packed FP32
+// FMA, two lanes' worth of fmaf in one instruction.
+__device__ __forceinline__ void ffma2(float &d0, float &d1, float a0, float a1, float b0,
+                                      float b1) {
+    asm("{\n\t.reg .b64 d, a, b;\n\t"
+        "mov.b64 a, {%2, %3};\n\t"
+        "mov.b64 b, {%4, %5};\n\t"
+        "mov.b64 d, {%0, %1};\n\t"
+        "fma.rn.f32x2 d, a, b, d;\n\t"
+        "mov.b64 {%0, %1}, d;\n}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
 // acc[j] += sum_c xv[gb(j) + c] * wv[j*CG + c]: the thread's 8 output
-// channels against the CG input channels of each one's group.
+// channels against the CG input channels of each one's group (one channel:
+// neighbouring channels pair up in packed FMAs).
 template <int CG>
 __device__ __forceinline__ void fma8(const float (&xv)[8], const float (&wv)[8 * CG],
                                      float (&acc)[8]) {
+    if constexpr (CG == 1) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int gb = (j / CG) * CG;  // first channel of j's group in the vector
+        for (int j = 0; j < 8; j += 2)
+            ffma2(acc[j], acc[j + 1], xv[j], xv[j + 1], wv[j], wv[j + 1]);
+    } else {
 #pragma unroll
-        for (int c = 0; c < CG; ++c) acc[j] = fmaf(xv[gb + c], wv[j * CG + c], acc[j]);
+        for (int j = 0; j < 8; ++j) {
+            const int gb = (j / CG) * CG;  // first channel of j's group in the vector
+#pragma unroll
+            for (int c = 0; c < CG; ++c) acc[j] = fmaf(xv[gb + c], wv[j * CG + c], acc[j]);
+        }
     }
 }
 
@@ -164,27 +184,34 @@ __device__ __forceinline__ void stage_filter(const Ti *w, float *wsm, int RS, in
 }
 
 // Accumulates filter row r into the thread's PX pixels x 8 channels. xrow
-// points at channel c0 of the row's column 0; pixel q0 + a, tap s reads
-// column (q0 + a)*v + s*dw - off. CHECK (global rows): columns outside
-// [0, W) and pixels at or past Q read zeros. Without CHECK the row is staged
-// in shared memory between zero padding columns (off = 0) wide enough for
-// every pixel of the last pixel block. SC > 0 (BF16 input only): the filter
+// (global rows) points at channel c0 of the row's column 0, xs (staged rows)
+// is its shared-memory address; pixel q0 + a, tap s reads column
+// (q0 + a)*v + s*dw - off. CHECK (global rows): columns outside [0, W) and
+// pixels at or past Q read zeros. Without CHECK the row is staged in shared
+// memory between zero padding columns (off = 0) wide enough for every pixel
+// of the last pixel block. SC > 0 (BF16 input only): the filter
 // width is the constant SC, so the row's loads are unrolled and issued
 // together. UNIT (horizontal stride and dilation 1): the PX pixels' SC taps
 // cover only PX + SC - 1 columns, each loaded (and, up to two channels per
 // group, converted to FP32) once.
 template <typename Ti, int CG, int SC, bool UNIT, int PX, bool CHECK>
-__device__ __forceinline__ void row_fma(const Ti *xrow, int q0, const DwParams &prm, int off,
-                                        const float4 *wt, int cv, float (&acc)[PX][8]) {
+__device__ __forceinline__ void row_fma(const Ti *xrow, uint32_t xs, int q0, const DwParams &prm,
+                                        int off, const float4 *wt, int cv, float (&acc)[PX][8]) {
     const int C = prm.C;
+    auto ld = [&](int col) {  // a BF16 channel vector of column col
+        if constexpr (CHECK) {
+            return ldraw(reinterpret_cast<const __nv_bfloat16 *>(xrow) + col * C);
+        } else {
+            return ldraw_s(xs + (uint32_t)(col * C * 2));
+        }
+    };
     if constexpr (SC > 0 && UNIT) {
         constexpr int NX = PX + SC - 1;
         uint4 xr[NX];
 #pragma unroll
         for (int e = 0; e < NX; ++e) {
             const int ww = q0 + e - off;
-            xr[e] = (!CHECK || (ww >= 0 && ww < prm.W)) ? ldraw<!CHECK>(xrow + ww * C)
-                                                        : make_uint4(0, 0, 0, 0);
+            xr[e] = (!CHECK || (ww >= 0 && ww < prm.W)) ? ld(ww) : make_uint4(0, 0, 0, 0);
         }
         if constexpr (CG <= 2) {
             float xv[NX][8];
@@ -218,7 +245,7 @@ __device__ __forceinline__ void row_fma(const Ti *xrow, int q0, const DwParams &
             for (int a = 0; a < PX; ++a) {
                 const int ww = (q0 + a) * prm.v + s * prm.dw - off;
                 xr[s][a] = (!CHECK || (q0 + a < prm.Q && ww >= 0 && ww < prm.W))
-                               ? ldraw<!CHECK>(xrow + ww * C)
+                               ? ld(ww)
                                : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
@@ -243,7 +270,7 @@ __device__ __forceinline__ void row_fma(const Ti *xrow, int q0, const DwParams &
                     if constexpr (CHECK) {
                         load8(xrow + (long long)ww * C, xv[a]);
                     } else {
-                        unpack8(ldraw<true>(xrow + ww * C), xv[a]);
+                        unpack8(ld(ww), xv[a]);
                     }
                 } else {
 #pragma unroll
@@ -320,7 +347,7 @@ __global__ void __launch_bounds__(DW_THREADS, Px<CG>::min_blocks) depthwise_kern
             const int h = p * prm.u + r * prm.dh - prm.ph;
             if (h < 0 || h >= prm.H) continue;
             const Ti *xrow = x + ((long long)n * prm.H + h) * prm.W * C + c0;
-            row_fma<Ti, CG, SC, UNIT, PX, true>(xrow, q0, prm, prm.pw,
+            row_fma<Ti, CG, SC, UNIT, PX, true>(xrow, 0, q0, prm, prm.pw,
                                                 wsm4 + r * prm.S * 2 * CG * cv + c0 / 8, cv, acc);
         }
         store_pixels<To, PX>(y, prm, n, p, q0, c0, acc);
@@ -408,7 +435,10 @@ __global__ void __launch_bounds__(DW_THREADS, 2) depthwise_staged_kernel(
     for (int b = blockIdx.x; b < prm.nbands; b += gridDim.x, ++it) {
         const int st = it & 1;
         const uint32_t par = (it >> 1) & 1;
-        const bool got = ptx::mbar_wait(&bar[st], par, lim, &zero);
+        // one thread polls; the others sleep in the block barrier, then
+        // observe the completed phase themselves (a single test each)
+        bool got = true;
+        if (tid == 0) got = ptx::mbar_wait(&bar[st], par, lim, &zero);
         if (__syncthreads_or(!got)) {
             // a copy did not complete in time: record it, wait (bounded) for
             // the copies this block still has in flight, and stop
@@ -422,9 +452,10 @@ __global__ void __launch_bounds__(DW_THREADS, 2) depthwise_staged_kernel(
             }
             return;
         }
+        if (tid != 0) ptx::mbar_try_wait(&bar[st], par);
         const int n = b / prm.bands_per_image, p0 = (b % prm.bands_per_image) * prm.TR;
         const int h0 = p0 * prm.u - prm.ph;
-        const __nv_bfloat16 *sx = stage0 + st * stage_elems;
+        const uint32_t sx = ptx::smem_addr(stage0 + st * stage_elems);
         for (unsigned i = tid; i < items; i += blockDim.x) {
             const int c0 = (int)(i % (unsigned)cv) * 8;
             const unsigned t = i / (unsigned)cv;
@@ -441,8 +472,8 @@ __global__ void __launch_bounds__(DW_THREADS, 2) depthwise_staged_kernel(
                 const int hr = pr * prm.u + r * prm.dh;
                 if (h0 + hr < 0 || h0 + hr >= prm.H) continue;
                 row_fma<__nv_bfloat16, CG, SC, UNIT, PX, false>(
-                    sx + hr * prm.WP * C + c0, q0, prm, 0, wsm4 + r * prm.S * 2 * CG * cv + c0 / 8,
-                    cv, acc);
+                    nullptr, sx + (uint32_t)((hr * prm.WP * C + c0) * 2), q0, prm, 0,
+                    wsm4 + r * prm.S * 2 * CG * cv + c0 / 8, cv, acc);
             }
             store_pixels<To, PX>(y, prm, n, p, q0, c0, acc);
         }
