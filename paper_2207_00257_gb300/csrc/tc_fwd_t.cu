@@ -26,10 +26,11 @@
 //    positions (Wx = power of two >= Q + max j; TR <= 256 / Wx, chosen to
 //    split the P rows into equal tiles), times KT output channels.
 //  * A operand: filter tile W[(r,s), c block] = KT rows of 128 bytes, resident
-//    in shared memory when the whole filter fits (loaded during the first
-//    tile, each phase's tiles right behind its band, with barriers per group
-//    of tiles so the first MMAs do not wait for the whole filter), otherwise
-//    streamed in table order.
+//    in shared memory when the whole filter fits (loaded once, with barriers
+//    per group of tiles so the first MMAs do not wait for the whole filter),
+//    otherwise streamed in table order through its own ring, whose stages
+//    hold up to four tiles each (one barrier wait and one commit per stage on
+//    the MMA thread: each costs it about as much as an MMA's worth of time).
 //  * B operand: 256 band rows starting at the tap's shift (K-major, 128-byte
 //    swizzle; any 128-byte row is a valid start).
 //  * TMEM: two 256-column accumulators. For M = 128 row k of D^T sits in lane
@@ -48,9 +49,14 @@
 //    (32x32b / 16x32bx2 loads), one 32-bit store per value; a warp's store
 //    covers consecutive channels of one position (two for M = 64).
 //
-// Warp roles and bounded waits as in tc_fwd.cu (576 threads: the epilogue of
-// one chunk is a chain of dependent steps, so more warps in flight keep the
-// tail of a CTA's last tile short).
+// Warp roles (608 threads): warp 0 loads the bands (one thread), warp 1
+// issues the MMAs (one thread), warps 2-17 run the epilogue (one chunk is a
+// chain of dependent steps, so more warps in flight keep the tail of a CTA's
+// last tile short), warp 18 loads the filter tiles. On GB300 a TMA load
+// occupies its issuing thread for roughly 100-250 ns whatever the box size,
+// and a single thread issuing bands and filter tiles in turn starved the MMA;
+// with two producers and one filter tile per lane the filter stream runs
+// ahead of the bands. Bounded waits as in tc_fwd.cu.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -66,7 +72,8 @@ namespace {
 constexpr int NPOS = 256;  // accumulator columns per tile (largest MMA N)
 constexpr int EPI_WARPS = 16;                 // four groups of four lane-quarter warps
 constexpr int EPI_GROUPS = EPI_WARPS / 4;
-constexpr int NTHREADS = 64 + 32 * EPI_WARPS;  // producer, MMA issuer, epilogue
+constexpr int FILTER_WARP = 2 + EPI_WARPS;      // after the epilogue warps
+constexpr int NTHREADS = 96 + 32 * EPI_WARPS;  // band producer, MMA issuer, epilogue, filter producer
 constexpr int SMEM_ALIGN = 1024;
 constexpr int BAR_BYTES = 1024;
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -102,6 +109,7 @@ struct TParams {
     uint16_t tap_shift[MAX_TAPS];  // band row offset i*Wx + j
     int c_blocks, k_tiles, p_tiles, num_tiles;
     int band_bytes, band_stride, w_resident, stages_a, stages_b;
+    int wgrp;  // streamed filter: tiles per ring stage (stages_b stages)
     int relu, out_f32;
     const float *bias, *x_scale, *w_scale;
     const float *alpha;  // fused per-channel scale (folded batch norm) or null
@@ -171,7 +179,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + SMEM_ALIGN - 1) & ~uintptr_t(SMEM_ALIGN - 1));
     const int SA = prm.stages_a, SB = prm.stages_b;
-    const int w_slots = prm.w_resident ? prm.RS * prm.c_blocks : SB;
+    const int WG = prm.wgrp;  // streamed filter tiles per stage
+    const int w_slots = prm.w_resident ? prm.RS * prm.c_blocks : SB * WG;
     uint8_t *sA = base;                              // band ring
     uint8_t *sW = sA + SA * prm.band_stride;         // filter tiles
     uint8_t *sEpi = sW + w_slots * W_TILE;           // staging
@@ -254,31 +263,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
     };
 
     if (warp == 0) {
+        // ------------------------------ band producer ------------------------------
         if (lane == 0) {
-            // ------------------------------ producer ------------------------------
             const bool skip = prm.guard.skip_loads != 0;
+            int sa = 0;
+            uint32_t pa = 0;
+            int issued_a = 0;
             bool ok = true;
-            int issued_w = 0;  // resident filter tiles issued (during the first tile)
-            int sa = 0, sb = 0;
-            uint32_t pa = 0, pb = 0;
-            int issued_a = 0, issued_b = 0;
-            if (OPH && prm.w_resident && !skip) {
-                // data gradient: the first tile uses one phase's taps only, so
-                // the whole resident filter is issued up front
-                for (int seq = 0; seq < w_tiles; ++seq) {
-                    const int b = seq / wper, cb = seq / prm.RS, ti = seq - cb * prm.RS;
-                    if (seq % wper == 0)
-                        ptx::mbar_arrive_expect_tx(
-                            &wres[b], (uint32_t)(min(wper, w_tiles - b * wper) * W_TILE));
-                    ptx::tma_load_3d(sW + seq * W_TILE, &prm.tmW, &wres[b], cb * KE, prm.tap_t[ti], 0);
-                }
-                issued_w = w_tiles;
-            }
             for (int tile = blockIdx.x; ok && tile < prm.num_tiles; tile += gridDim.x) {
                 const Tile T = tdecode<OPH>(prm, tile);
-                const int n = T.n, p0 = T.p0, kt = T.kt;
+                const int n = T.n, p0 = T.p0;
                 for (int cb = 0; ok && cb < prm.c_blocks; ++cb) {
-                    for (int f = T.f0; ok && f < T.f1; ++f) {
+                    for (int f = T.f0; f < T.f1; ++f) {
                         if (!ptx::mbar_wait(&emptyA[sa], pa ^ 1, lim, abort_flag)) {
                             fail();
                             ok = false;
@@ -298,66 +294,97 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                             sa = 0;
                             pa ^= 1;
                         }
-                        if (prm.w_resident) {
-                            // first tile: this phase's filter tiles, right behind its band
-                            if (skip || issued_w == w_tiles) continue;
-                            for (int ti = f ? prm.ph_end[f - 1] : 0; ti < prm.ph_end[f]; ++ti) {
-                                const int seq = cb * prm.RS + ti, b = seq / wper;
-                                if (seq % wper == 0)
-                                    ptx::mbar_arrive_expect_tx(
-                                        &wres[b], (uint32_t)(min(wper, w_tiles - b * wper) * W_TILE));
-                                ptx::tma_load_3d(sW + seq * W_TILE, &prm.tmW, &wres[b], cb * KE,
-                                                 prm.tap_t[ti], 0);
-                                ++issued_w;
-                            }
-                            continue;
-                        }
-                        for (int ti = f ? prm.ph_end[f - 1] : 0; ti < prm.ph_end[f]; ++ti) {
-                            if (!ptx::mbar_wait(&emptyW[sb], pb ^ 1, lim, abort_flag)) {
-                                fail();
-                                ok = false;
-                                break;
-                            }
-                            if (!skip) {
-                                ptx::mbar_arrive_expect_tx(&fullW[sb], (uint32_t)W_TILE);
-                                ptx::tma_load_3d(sW + sb * W_TILE, &prm.tmW, &fullW[sb], cb * KE,
-                                                 prm.tap_t[ti], kt * KT);
-                                ++issued_b;
-                            }
-                            if (++sb == SB) {
-                                sb = 0;
-                                pb ^= 1;
-                            }
-                        }
                     }
                 }
             }
             volatile int zero = 0;
-            {
-                int st = sa;
-                uint32_t ph = pa;
-                for (int i = 0; i < min(issued_a, SA); ++i) {
-                    if (st == 0) {
-                        st = SA;
-                        ph ^= 1;
+            int st = sa;
+            uint32_t ph = pa;
+            for (int i = 0; i < min(issued_a, SA); ++i) {
+                if (st == 0) {
+                    st = SA;
+                    ph ^= 1;
+                }
+                --st;
+                if (!ptx::mbar_wait(&fullA[st], ph, lim, &zero)) fail();
+            }
+        }
+    } else if (warp == FILTER_WARP) {
+        // ----------------------------- filter producer -----------------------------
+        // Its own warp, so the filter stream runs ahead of the bands by as many
+        // tiles as its ring holds. A TMA load costs its issuing thread about as
+        // long as a 32 KB box takes to arrive, so the tiles are issued by one
+        // lane each, in parallel. All lanes keep the same counters.
+        const unsigned FULL = 0xffffffffu;
+        const bool skip = prm.guard.skip_loads != 0;
+        bool ok = true;
+        int issued_w = 0;  // resident filter tiles issued
+        long long wq = 0;  // filter tiles that went through the streamed ring
+        long long issued_b = 0;
+        if (prm.w_resident) {
+            // Resident filter: every tile once, in storage order (= MMA order),
+            // one per lane; each group's byte count is announced on its barrier
+            // (by the lane holding the group's first tile) before any load.
+            for (int s0 = 0; !skip && s0 < w_tiles; s0 += 32) {
+                const int seq = s0 + lane;
+                const bool act = seq < w_tiles;
+                if (act && seq % wper == 0) {
+                    const int g = seq / wper;
+                    ptx::mbar_arrive_expect_tx(&wres[g],
+                                               (uint32_t)(min(wper, w_tiles - g * wper) * W_TILE));
+                }
+                __syncwarp();
+                if (act) {
+                    const int cb = seq / prm.RS;
+                    ptx::tma_load_3d(sW + seq * W_TILE, &prm.tmW, &wres[seq / wper], cb * KE,
+                                     prm.tap_t[seq - cb * prm.RS], 0);
+                }
+                __syncwarp();
+            }
+            issued_w = skip ? 0 : w_tiles;
+        } else {
+            // Streamed filter: a tile's filter sequence (channel block, then the
+            // taps of its phases) in stages of WG tiles, one barrier pair per
+            // stage, one tile per lane; a tile's last stage may be partial.
+            for (int tile = blockIdx.x; ok && tile < prm.num_tiles; tile += gridDim.x) {
+                const Tile T = tdecode<OPH>(prm, tile);
+                const int t0 = T.f0 ? prm.ph_end[T.f0 - 1] : 0;
+                const int ntp = prm.ph_end[T.f1 - 1] - t0;  // taps per channel block
+                const int ntile = prm.c_blocks * ntp;
+                for (int j0 = 0; j0 < ntile; j0 += WG, ++wq) {
+                    const int cnt = min(WG, ntile - j0);
+                    const int stage = (int)(wq % SB);
+                    int wok = 1;
+                    if (lane == 0) {
+                        wok = ptx::mbar_wait(&emptyW[stage], (uint32_t)((wq / SB) & 1) ^ 1u, lim,
+                                             abort_flag);
+                        if (wok && !skip)
+                            ptx::mbar_arrive_expect_tx(&fullW[stage], (uint32_t)(cnt * W_TILE));
                     }
-                    --st;
-                    if (!ptx::mbar_wait(&fullA[st], ph, lim, &zero)) fail();
+                    if (!__shfl_sync(FULL, wok, 0)) {
+                        if (lane == 0) fail();
+                        ok = false;
+                        break;
+                    }
+                    if (!skip) {
+                        if (lane < cnt) {
+                            const int j = j0 + lane, cb = j / ntp;
+                            ptx::tma_load_3d(sW + (stage * WG + lane) * W_TILE, &prm.tmW, &fullW[stage],
+                                             cb * KE, prm.tap_t[t0 + j - cb * ntp], T.kt * KT);
+                        }
+                        ++issued_b;
+                    }
                 }
             }
-            {
-                int st = sb;
-                uint32_t ph = pb;
-                for (int i = 0; i < min(issued_b, SB); ++i) {
-                    if (st == 0) {
-                        st = SB;
-                        ph ^= 1;
-                    }
-                    --st;
-                    if (!ptx::mbar_wait(&fullW[st], ph, lim, &zero)) fail();
-                }
+        }
+        if (lane == 0) {
+            volatile int zero = 0;
+            // the last load of every streamed filter stage
+            for (long long i = 1; i <= (issued_b < SB ? issued_b : (long long)SB); ++i) {
+                const long long u = wq - i;
+                if (!ptx::mbar_wait(&fullW[(int)(u % SB)], (uint32_t)((u / SB) & 1), lim, &zero)) fail();
             }
-            // resident filter groups fully issued (a group is complete only when all its tiles were)
+            // resident filter groups
             for (int b = 0; b * wper < issued_w; ++b)
                 if (!ptx::mbar_wait(&wres[b], 0, lim, &zero)) fail();
         }
@@ -367,6 +394,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
             bool ok = true;
             uint32_t idesc = FP8 ? ptx::idesc_e4m3(prm.n_pos) : ptx::idesc_bf16(prm.n_pos);
             idesc = (idesc & ~(0x1Fu << 24)) | ((uint32_t)(KT >> 4) << 24);  // M = KT
+            const uint64_t adb = ptx::sdesc_kmajor_sw128(ptx::smem_addr(sW));  // filter slot 0
             int sa = 0, sb = 0;
             uint32_t pa = 0, pb = 0;
             uint32_t wres_seen = 0;  // resident filter groups already waited for
@@ -379,27 +407,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                     break;
                 }
                 ptx::tc_fence_after();
-                const Tile T = tdecode<OPH>(prm, tile);
+                // only a data-gradient tile restricts the phases; the forward uses all
+                int f0 = 0, f1 = prm.n_phase;
+                if constexpr (OPH) {
+                    const Tile T = tdecode<OPH>(prm, tile);
+                    f0 = T.f0;
+                    f1 = T.f1;
+                }
                 const uint32_t d = tmem_base + (uint32_t)(acc * NPOS);
                 uint32_t accum = 0;
+                // streamed filter: tiles used so far in this tile, and the position
+                // inside the current stage of WG tiles
+                const int ntile = prm.c_blocks * (prm.ph_end[f1 - 1] - (f0 ? prm.ph_end[f0 - 1] : 0));
+                int jw = 0, gi = 0;
                 for (int cb = 0; ok && cb < prm.c_blocks; ++cb) {
-                    for (int f = T.f0; f < T.f1; ++f) {
+                    for (int f = f0; f < f1; ++f) {
                         if (!ptx::mbar_wait(&fullA[sa], pa, lim, abort_flag)) {
                             fail();
                             ok = false;
                             break;
                         }
                         ptx::tc_fence_after();
-                        const uint32_t band = ptx::smem_addr(sA + sa * prm.band_stride);
-                        for (int ti = f ? prm.ph_end[f - 1] : 0; ti < prm.ph_end[f]; ++ti) {
-                            uint32_t w_addr;
-                            if (prm.w_resident) {
-                                const int seq = cb * prm.RS + ti;
-                                // the forward's first tile uses every group; a data-gradient
-                                // tile uses its phase's groups, first seen on any tile
-                                if (local == 0 || OPH) {
-                                    const int grp = seq / wper;
-                                    if (!((wres_seen >> grp) & 1u)) {  // first use of this group
+                        // Descriptors are built once per band; a tap adds its row shift
+                        // (128 bytes = 8 descriptor units per row) to the band's and, for a
+                        // resident filter, steps one filter tile (tiles are stored in the
+                        // order the MMAs use them). The start-address field cannot carry:
+                        // shared addresses stay below 256 KB.
+                        const uint64_t bdb =
+                            ptx::sdesc_kmajor_sw128(ptx::smem_addr(sA + sa * prm.band_stride));
+                        const int t0 = f ? prm.ph_end[f - 1] : 0, t1 = prm.ph_end[f];
+                        if (prm.w_resident) {
+                            const bool first_use = local == 0 || OPH;
+                            uint64_t ad = adb + (uint64_t)((cb * prm.RS + t0) * (W_TILE >> 4));
+                            for (int ti = t0; ti < t1; ++ti) {
+                                if (first_use) {
+                                    // the forward's first tile uses every group; a data-gradient
+                                    // tile uses its phase's groups, first seen on any tile
+                                    const int grp = (cb * prm.RS + ti) / wper;
+                                    if (!((wres_seen >> grp) & 1u)) {
                                         if (!ptx::mbar_wait(&wres[grp], 0, lim, abort_flag)) {
                                             fail();
                                             ok = false;
@@ -409,32 +454,45 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
                                         wres_seen |= 1u << grp;
                                     }
                                 }
-                                w_addr = ptx::smem_addr(sW + seq * W_TILE);
-                            } else {
-                                if (!ptx::mbar_wait(&fullW[sb], pb, lim, abort_flag)) {
-                                    fail();
-                                    ok = false;
-                                    break;
-                                }
-                                ptx::tc_fence_after();
-                                w_addr = ptx::smem_addr(sW + sb * W_TILE);
-                            }
-                            const uint64_t ad = ptx::sdesc_kmajor_sw128(w_addr);
-                            const uint64_t bd =
-                                ptx::sdesc_kmajor_sw128(band + (uint32_t)prm.tap_shift[ti] * 128u);
+                                const uint64_t bd = bdb + ((uint64_t)prm.tap_shift[ti] << 3);
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                if (FP8)
-                                    ptx::mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, accum);
-                                else
-                                    ptx::mma_f16(d, ad + 2 * k, bd + 2 * k, idesc, accum);
-                                accum = 1;
+                                for (int k = 0; k < 4; ++k) {
+                                    if (FP8)
+                                        ptx::mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                                    else
+                                        ptx::mma_f16(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                                    accum = 1;
+                                }
+                                ad += W_TILE >> 4;
                             }
-                            if (!prm.w_resident) {
-                                ptx::mma_commit(&emptyW[sb]);
-                                if (++sb == SB) {
-                                    sb = 0;
-                                    pb ^= 1;
+                        } else {
+                            for (int ti = t0; ti < t1; ++ti) {
+                                if (gi == 0) {  // first tile of a stage
+                                    if (!ptx::mbar_wait(&fullW[sb], pb, lim, abort_flag)) {
+                                        fail();
+                                        ok = false;
+                                        break;
+                                    }
+                                    ptx::tc_fence_after();
+                                }
+                                const uint64_t ad = adb + (uint64_t)((sb * WG + gi) * (W_TILE >> 4));
+                                const uint64_t bd = bdb + ((uint64_t)prm.tap_shift[ti] << 3);
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    if (FP8)
+                                        ptx::mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                                    else
+                                        ptx::mma_f16(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                                    accum = 1;
+                                }
+                                ++jw;
+                                if (++gi == WG || jw == ntile) {  // stage used up
+                                    ptx::mma_commit(&emptyW[sb]);
+                                    gi = 0;
+                                    if (++sb == SB) {
+                                        sb = 0;
+                                        pb ^= 1;
+                                    }
                                 }
                             }
                         }
@@ -672,6 +730,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_cons
 
 struct TPlan {
     int wx_log2, TR, nr, band_bytes, band_stride, c_blocks, w_resident, stages_a, stages_b;
+    int wgrp;  // streamed filter tiles per ring stage
     int n_phase;
     int flat, n_pos, k_tiles;
     long long num_tiles;
@@ -777,11 +836,18 @@ bool plan_memory(int kt, long long w_tiles, TPlan *pl, TPlan &p) {
         p.w_resident = 1;
         p.stages_a = (int)std::min<long long>(MAX_SA, (budget - w_total) / p.band_stride);
         p.stages_b = 0;
+        p.wgrp = 1;
     } else {
+        // a third band stage when the filter ring keeps at least 4 slots: a band
+        // comes from HBM, a filter tile from L2, so bands need the longer lead
         p.w_resident = 0;
-        p.stages_a = 2;
-        p.stages_b = std::min(MAX_SB, (budget - 2 * p.band_stride) / wtile);
-        if (p.stages_b < 2) return false;
+        p.stages_a = (budget - 3 * p.band_stride) / wtile >= 4 ? 3 : 2;
+        const int slots = std::min(MAX_SB, (budget - p.stages_a * p.band_stride) / wtile);
+        if (slots < 2) return false;
+        // stages of up to 4 tiles (one barrier wait and one commit per stage on
+        // the MMA thread), at least two stages
+        p.wgrp = slots >= 8 ? 4 : slots >= 6 ? 3 : slots >= 4 ? 2 : 1;
+        p.stages_b = slots / p.wgrp;
     }
     *pl = p;
     return true;
@@ -908,6 +974,7 @@ gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, con
     prm.w_resident = pl.w_resident;
     prm.stages_a = pl.stages_a;
     prm.stages_b = pl.stages_b;
+    prm.wgrp = pl.wgrp;
     prm.relu = (d.flags & GBCONV_FLAG_RELU) ? 1 : 0;
     prm.out_f32 = of32;
     prm.bias = (d.flags & GBCONV_FLAG_BIAS) ? bias : nullptr;
@@ -917,7 +984,7 @@ gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, con
     prm.z = fz.z;
     prm.guard = make_guard();
     if (!prm.guard.err) return GBCONV_ERR_CUDA;
-    const int w_slots = pl.w_resident ? d.R * d.S * pl.c_blocks : pl.stages_b;
+    const int w_slots = pl.w_resident ? d.R * d.S * pl.c_blocks : pl.stages_b * pl.wgrp;
     const size_t smem = (size_t)SMEM_ALIGN + (size_t)pl.stages_a * pl.band_stride +
                         (size_t)w_slots * kt * 128 +
                         (kt == 128 ? epi_total<128>() : epi_total<64>()) + BAR_BYTES;
@@ -1137,10 +1204,11 @@ gbconv_status_t launch_tc_dgrad_t(const Dims &d, const void *dy, const void *wT,
     prm.w_resident = pl.w_resident;
     prm.stages_a = pl.stages_a;
     prm.stages_b = pl.stages_b;
+    prm.wgrp = pl.wgrp;
     prm.out_f32 = d.out_dtype == GBCONV_F32;
     prm.guard = make_guard();
     if (!prm.guard.err) return GBCONV_ERR_CUDA;
-    const int w_slots = pl.w_resident ? nt * pl.c_blocks : pl.stages_b;
+    const int w_slots = pl.w_resident ? nt * pl.c_blocks : pl.stages_b * pl.wgrp;
     const size_t smem = (size_t)SMEM_ALIGN + (size_t)pl.stages_a * pl.band_stride +
                         (size_t)w_slots * kt * 128 +
                         (kt == 128 ? epi_total<128>() : epi_total<64>()) + BAR_BYTES;
