@@ -80,6 +80,77 @@ __global__ void __launch_bounds__(256) bias_grad_nhwc(const T *__restrict__ g, l
     }
 }
 
+// NHWC BF16 with K a power of two from 8 to 4096: thread t owns the
+// channel octet o = t % (K/8) (one 16-byte load per row) and the rows
+// r0 + t/(K/8) + i*(512/(K/8)) of block y's slice, eight loads in flight,
+// eight compensated running sums; the block then joins the row phases of
+// each channel in fixed order. The 64-byte warp loads of bias_grad_nhwc kept
+// too few bytes in flight to stream the tensor.
+__device__ __forceinline__ void widen_bf16x2(uint32_t v, float &lo, float &hi) {
+    lo = __uint_as_float(v << 16);
+    hi = __uint_as_float(v & 0xffff0000u);
+}
+
+__global__ void __launch_bounds__(512) bias_grad_nhwc_bf16x8(const __nv_bfloat16 *__restrict__ g,
+                                                              long long M, int K, int slices,
+                                                              float *__restrict__ part) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
+    constexpr int UNROLL = 8;
+    __shared__ float sh[512 * 8];  // [row phase][K]: 512/(K/8) x K floats
+    const int oct = K >> 3;
+    const int o = threadIdx.x % oct, rp = threadIdx.x / oct, rstep = 512 / oct;
+    const long long r0 = M * blockIdx.x / slices, r1 = M * (blockIdx.x + 1) / slices;
+    float sum[8], comp[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sum[e] = comp[e] = 0.f;
+    const uint4 *gv = reinterpret_cast<const uint4 *>(g);
+    auto add = [&](const uint4 &v) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float lo, hi;
+            widen_bf16x2(w[i], lo, hi);
+            neumaier(sum[2 * i], comp[2 * i], lo);
+            neumaier(sum[2 * i + 1], comp[2 * i + 1], hi);
+        }
+    };
+    long long r = r0 + rp;
+    for (; r + (long long)(UNROLL - 1) * rstep < r1; r += (long long)UNROLL * rstep) {
+        uint4 v[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) v[u] = __ldg(gv + (r + (long long)u * rstep) * oct + o);
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) add(v[u]);
+    }
+    for (; r < r1; r += rstep) add(__ldg(gv + r * oct + o));
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sh[rp * K + o * 8 + e] = sum[e] + comp[e];
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += 512) {
+        float s2 = 0.f, c2 = 0.f;
+        for (int p = 0; p < rstep; ++p) neumaier(s2, c2, sh[p * K + k]);
+        part[(long long)blockIdx.x * K + k] = s2 + c2;
+    }
+}
+
+// out[i] = sum over slices of ws[s][i] for a short vector (one warp per
+// output): lanes take slices lane, lane + 32, ... with compensated sums, then
+// a fixed-shape shuffle tree.
+__global__ void reduce_slices_warp(const float *__restrict__ ws, int slices, int n,
+                                   float *__restrict__ out) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
+    const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;  // whole warps
+    float sum = 0.f, comp = 0.f;
+    for (int s = lane; s < slices; s += 32) neumaier(sum, comp, ws[(long long)s * n + i]);
+    float t = sum + comp;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    if (lane == 0) out[i] = t;
+}
+
 // NCHW: g is [N][K][P*Q]; block (k, slice over n) reduces its rows with a
 // fixed-shape tree, then writes one partial.
 template <typename T>
@@ -318,6 +389,15 @@ gbconv_status_t launch_reduce_slices(const float *ws, int slices, long long n, f
 gbconv_status_t launch_bias_grad(const Dims &d, const void *g, float *db, float *ws, int slices,
                                  cudaStream_t st) {
     cudaError_t e;
+    const bool pow2 = d.K >= 8 && d.K <= 4096 && (d.K & (d.K - 1)) == 0;
+    if (d.layout == GBCONV_NHWC && d.in_dtype == GBCONV_BF16 && pow2 &&
+        (reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+        e = launch_pdl(bias_grad_nhwc_bf16x8, dim3((unsigned)slices), dim3(512), 0, st,
+                       (const __nv_bfloat16 *)g, d.M(), d.K, slices, ws);
+        if (e != cudaSuccess) return cuda_status(e);
+        return cuda_status(launch_pdl(reduce_slices_warp, dim3((unsigned)((d.K + 7) / 8)), dim3(256), 0,
+                                      st, (const float *)ws, slices, d.K, db));
+    }
     if (d.layout == GBCONV_NHWC) {
         dim3 grid((unsigned)((d.K + 31) / 32), (unsigned)slices);
         if (d.in_dtype == GBCONV_F32)

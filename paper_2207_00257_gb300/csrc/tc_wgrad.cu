@@ -18,8 +18,9 @@
 // the workspace [slice][K][R][S][C]; a second kernel adds the slices in fixed
 // order with compensated summation.
 //
-// Warp roles (192 threads): warp 0 producer, warp 1 MMA issuer, warps 2-5
-// epilogue (one TMEM lane quarter each). All waits are bounded.
+// Warp roles (224 threads): warps 0 and 6 producers (alternate reduction
+// steps, one box per lane), warp 1 MMA issuer, warps 2-5 epilogue (one TMEM
+// lane quarter each). All waits are bounded.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -36,7 +37,8 @@ constexpr int KT = 128;              // output-channel tile = MMA M
 constexpr int PIX = 64;              // pixels per reduction step
 constexpr int ATOM = PIX * 128;      // 64 pixel rows x 128 B = one 64-channel block
 constexpr int A_STAGE = 2 * ATOM;    // dy for 128 output channels
-constexpr int NTHREADS = 192;
+constexpr int NTHREADS = 224;
+constexpr int PRODUCER2 = 6;        // second producer warp, after the epilogue warps
 constexpr int EPI_WARPS = 4;
 constexpr int EPI_BYTES = 8192;      // two 4 KB FP32 chunk buffers per epilogue warp
 constexpr int EPI_TOTAL = EPI_WARPS * EPI_BYTES;
@@ -128,61 +130,62 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_wgrad_kernel(const __grid_cons
         b1 = (int)((long long)prm.nblocks * (slice + 1) / prm.slices);
     };
 
-    if (warp == 0) {
-        if (lane == 0) {
-            // ------------------------------ producer ------------------------------
-            int stage = 0;
-            uint32_t phase = 0;
-            int issued = 0;
-            bool ok = true;
-            const uint32_t bytes = A_STAGE + B_STAGE;
-            for (int u = blockIdx.x; ok && u < prm.units; u += gridDim.x) {
-                int slice, kt, rs, ct, b0, b1;
-                unit_decode(prm, u, slice, kt, rs, ct);
-                block_range(slice, b0, b1);
-                const int r = rs / prm.S, s = rs - r * prm.S;
-                for (int b = b0; b < b1; ++b) {
-                    const int m0 = b * PIX;
+    if (warp == 0 || warp == PRODUCER2) {
+        // ------------------------------ producers ------------------------------
+        // Two warps take alternate reduction steps (ring stages); within a
+        // step each box is issued by its own lane. On GB300 a TMA load holds
+        // its issuing thread about as long as an 8 KB box takes to arrive, so
+        // one thread issuing four boxes per step starved the MMAs.
+        const unsigned FULL = 0xffffffffu;
+        const int me = warp == 0 ? 0 : 1;
+        const bool skip = prm.guard.skip_loads != 0;
+        constexpr int NBOX = 2 + BN / 64;  // dy: two 64-channel halves; x: BN / 64 blocks
+        const uint32_t bytes = A_STAGE + B_STAGE;
+        long long it = 0;        // reduction steps of this CTA so far (both warps)
+        long long last = -1;     // last step this warp issued
+        bool ok = true;
+        for (int u = blockIdx.x; ok && u < prm.units; u += gridDim.x) {
+            int slice, kt, rs, ct, b0, b1;
+            unit_decode(prm, u, slice, kt, rs, ct);
+            block_range(slice, b0, b1);
+            const int r = rs / prm.S, s = rs - r * prm.S;
+            for (int b = b0; b < b1; ++b, ++it) {
+                if ((int)(it & 1) != me) continue;
+                const int stage = (int)(it % stages);
+                const uint32_t phase = (uint32_t)((it / stages) & 1);
+                int wok = 1;
+                if (lane == 0) {
+                    wok = ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort_flag);
+                    if (wok && !skip) ptx::mbar_arrive_expect_tx(&full[stage], bytes);
+                }
+                if (!__shfl_sync(FULL, wok, 0)) {
+                    if (lane == 0) fail();
+                    ok = false;
+                    break;
+                }
+                if (skip) continue;
+                const int m0 = b * PIX;
+                if (lane < 2) {
+                    ptx::tma_load_2d(sA + stage * A_STAGE + lane * ATOM, &prm.tmG, &full[stage],
+                                     kt * KT + 64 * lane, m0);
+                } else if (lane < NBOX) {
+                    const int j = lane - 2;
                     const int q = m0 % prm.Q, t = m0 / prm.Q;
                     const int p = t % prm.P, n = t / prm.P;
-                    if (!ptx::mbar_wait(&empty[stage], phase ^ 1, lim, abort_flag)) {
-                        fail();
-                        ok = false;
-                        break;
-                    }
-                    if (!prm.guard.skip_loads) {
-                        ptx::mbar_arrive_expect_tx(&full[stage], bytes);
-                        uint8_t *a = sA + stage * A_STAGE;
-                        ptx::tma_load_2d(a, &prm.tmG, &full[stage], kt * KT, m0);
-                        ptx::tma_load_2d(a + ATOM, &prm.tmG, &full[stage], kt * KT + 64, m0);
-                        uint8_t *bb = sB + stage * B_STAGE;
-#pragma unroll
-                        for (int j = 0; j < BN / 64; ++j)
-                            ptx::tma_load_im2col_4d(bb + j * ATOM, &prm.tmX, &full[stage],
-                                                    ct * BN + j * 64, q * prm.v - prm.pw,
-                                                    p * prm.u - prm.ph, n, (uint16_t)(s * prm.dw),
-                                                    (uint16_t)(r * prm.dh));
-                        ++issued;
-                    }
-                    if (++stage == stages) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
+                    ptx::tma_load_im2col_4d(sB + stage * B_STAGE + j * ATOM, &prm.tmX, &full[stage],
+                                            ct * BN + j * 64, q * prm.v - prm.pw, p * prm.u - prm.ph,
+                                            n, (uint16_t)(s * prm.dw), (uint16_t)(r * prm.dh));
                 }
+                last = it;
             }
-            int st = stage;
-            uint32_t ph = phase;
-            for (int i = 0; i < min(issued, stages); ++i) {
-                if (st == 0) {
-                    st = stages;
-                    ph ^= 1;
-                }
-                --st;
-                if (!ptx::mbar_wait(&full[st], ph, lim, abort_flag)) {
-                    volatile int zero = 0;
-                    if (!ptx::mbar_wait(&full[st], ph, lim, &zero)) fail();
-                }
-            }
+        }
+        // this warp's steps among the last `stages` steps of the CTA are the
+        // ones that may still be in flight (an earlier step's slot was reused)
+        if (lane == 0) {
+            volatile int zero = 0;
+            for (long long j = last; j >= 0 && j >= it - stages; j -= 2)
+                if (!ptx::mbar_wait(&full[(int)(j % stages)], (uint32_t)((j / stages) & 1), lim, &zero))
+                    fail();
         }
     } else if (warp == 1) {
         if (lane == 0) {
