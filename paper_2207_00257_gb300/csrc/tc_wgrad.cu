@@ -18,8 +18,8 @@
 // the workspace [slice][K][R][S][C]; a second kernel adds the slices in fixed
 // order with compensated summation.
 //
-// Warp roles (224 threads): warps 0 and 6 producers (alternate reduction
-// steps, one box per lane), warp 1 MMA issuer, warps 2-5 epilogue (one TMEM
+// Warp roles (288 threads): warps 0 and 6-8 producers (reduction steps taken
+// in turn, one box per lane), warp 1 MMA issuer, warps 2-5 epilogue (one TMEM
 // lane quarter each). All waits are bounded.
 #include <cuda_bf16.h>
 
@@ -37,8 +37,8 @@ constexpr int KT = 128;              // output-channel tile = MMA M
 constexpr int PIX = 64;              // pixels per reduction step
 constexpr int ATOM = PIX * 128;      // 64 pixel rows x 128 B = one 64-channel block
 constexpr int A_STAGE = 2 * ATOM;    // dy for 128 output channels
-constexpr int NTHREADS = 224;
-constexpr int PRODUCER2 = 6;        // second producer warp, after the epilogue warps
+constexpr int NPROD = 4;             // producer warps: 0 and 6 .. 4 + NPROD
+constexpr int NTHREADS = 64 + 32 * 4 + 32 * (NPROD - 1);
 constexpr int EPI_WARPS = 4;
 constexpr int EPI_BYTES = 8192;      // two 4 KB FP32 chunk buffers per epilogue warp
 constexpr int EPI_TOTAL = EPI_WARPS * EPI_BYTES;
@@ -130,14 +130,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_wgrad_kernel(const __grid_cons
         b1 = (int)((long long)prm.nblocks * (slice + 1) / prm.slices);
     };
 
-    if (warp == 0 || warp == PRODUCER2) {
+    if (warp == 0 || warp >= 6) {
         // ------------------------------ producers ------------------------------
-        // Two warps take alternate reduction steps (ring stages); within a
-        // step each box is issued by its own lane. On GB300 a TMA load holds
+        // The producer warps take the reduction steps (ring stages) in turn;
+        // within a step each box is issued by its own lane. On GB300 a TMA load holds
         // its issuing thread about as long as an 8 KB box takes to arrive, so
         // one thread issuing four boxes per step starved the MMAs.
         const unsigned FULL = 0xffffffffu;
-        const int me = warp == 0 ? 0 : 1;
+        const int me = warp == 0 ? 0 : warp - 5;
         const bool skip = prm.guard.skip_loads != 0;
         constexpr int NBOX = 2 + BN / 64;  // dy: two 64-channel halves; x: BN / 64 blocks
         const uint32_t bytes = A_STAGE + B_STAGE;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_wgrad_kernel(const __grid_cons
             block_range(slice, b0, b1);
             const int r = rs / prm.S, s = rs - r * prm.S;
             for (int b = b0; b < b1; ++b, ++it) {
-                if ((int)(it & 1) != me) continue;
+                if ((int)(it % NPROD) != me) continue;
                 const int stage = (int)(it % stages);
                 const uint32_t phase = (uint32_t)((it / stages) & 1);
                 int wok = 1;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_wgrad_kernel(const __grid_cons
         // ones that may still be in flight (an earlier step's slot was reused)
         if (lane == 0) {
             volatile int zero = 0;
-            for (long long j = last; j >= 0 && j >= it - stages; j -= 2)
+            for (long long j = last; j >= 0 && j >= it - stages; j -= NPROD)
                 if (!ptx::mbar_wait(&full[(int)(j % stages)], (uint32_t)((j / stages) & 1), lim, &zero))
                     fail();
         }
