@@ -221,10 +221,8 @@ def replay_timed(g, torch, dist_on):
 def max_over_ranks(v, torch, dist_on):
     if not dist_on:
         return v
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2207_00257_gb300.distributed import max_over_ranks as mor
+    return mor(v, device="cuda")
 
 
 def bench_layers(layers, steps, warmup, nsets, torch, dist_on, sampler=None):
@@ -319,7 +317,8 @@ def run_ours(args, rank, world, local):
     time.sleep(0.3)
     res = bench_layers(layers, args.steps, args.warmup, nsets, torch, dist_on)
     flops_step = sum(l.sh.flops for l in layers)
-    value = flops_step * args.steps * world / (res["ms_total"] * 1e-3) / 1e12
+    from paper_2207_00257_gb300.distributed import weak_scaling_rate
+    value = weak_scaling_rate(flops_step * args.steps, world, res["ms_total"] * 1e-3) / 1e12
     per_layer = resnet_report(layers, res, pk, 2)
     # Each layer alone, K launches back to back in one graph (programmatic
     # launch overlapping consecutive launches): the per-layer cost inside the
