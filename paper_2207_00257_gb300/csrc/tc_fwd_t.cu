@@ -49,10 +49,12 @@
 //    (32x32b / 16x32bx2 loads), one 32-bit store per value; a warp's store
 //    covers consecutive channels of one position (two for M = 64).
 //
-// Warp roles (608 threads): warp 0 loads the bands (one thread), warp 1
-// issues the MMAs (one thread), warps 2-17 run the epilogue (one chunk is a
-// chain of dependent steps, so more warps in flight keep the tail of a CTA's
-// last tile short), warp 18 loads the filter tiles. On GB300 a TMA load
+// Warp roles: warp 0 loads the bands (one thread), warp 1 issues the MMAs
+// (one thread), then the epilogue warps (16 for 128-channel tiles, 8 for
+// 64-channel tiles: one chunk is a chain of dependent steps, so more warps in
+// flight keep the tail of a CTA's last tile short, while fewer leave more
+// issue slots to the MMA thread; for 64-channel tiles 8 measured 2.5 %
+// faster), then one warp that loads the filter tiles. On GB300 a TMA load
 // occupies its issuing thread for roughly 100-250 ns whatever the box size,
 // and a single thread issuing bands and filter tiles in turn starved the MMA;
 // with two producers and one filter tile per lane the filter stream runs
@@ -70,10 +72,15 @@ namespace gbc {
 namespace {
 
 constexpr int NPOS = 256;  // accumulator columns per tile (largest MMA N)
-constexpr int EPI_WARPS = 16;                 // four groups of four lane-quarter warps
-constexpr int EPI_GROUPS = EPI_WARPS / 4;
-constexpr int FILTER_WARP = 2 + EPI_WARPS;      // after the epilogue warps
-constexpr int NTHREADS = 96 + 32 * EPI_WARPS;  // band producer, MMA issuer, epilogue, filter producer
+// Epilogue warps (groups of four lane-quarter warps): 16 for 128-channel
+// tiles; 8 for 64-channel tiles, whose epilogue has half the data, so that
+// fewer warps share the MMA-issuing thread's sub-partition while the next
+// tile's MMAs are issued.
+template <int KT>
+__host__ __device__ constexpr int epi_warps() { return KT == 64 ? 8 : 16; }
+// band producer, MMA issuer, epilogue, filter producer
+template <int KT>
+__host__ __device__ constexpr int nthreads() { return 96 + 32 * epi_warps<KT>(); }
 constexpr int SMEM_ALIGN = 1024;
 constexpr int BAR_BYTES = 1024;
 constexpr int SMEM_LIMIT = 227 * 1024;
@@ -164,7 +171,10 @@ __device__ __forceinline__ Tile tdecode(const TParams &p, int tile) {
 // FUSED: the epilogue also applies the per-channel scale and the residual.
 // OPH: data-gradient launch, tiles grouped by output phase (n_ophase > 0).
 template <int KT, bool FP8, bool FUSED, bool OPH>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_fwd_t_kernel(const __grid_constant__ TParams prm) {
+__global__ void __launch_bounds__(nthreads<KT>(), 1) tc_fwd_t_kernel(const __grid_constant__ TParams prm) {
+    constexpr int EPI_WARPS = epi_warps<KT>();
+    constexpr int EPI_GROUPS = EPI_WARPS / 4;
+    constexpr int FILTER_WARP = 2 + EPI_WARPS;  // after the epilogue warps
     constexpr int KE = FP8 ? 128 : 64;
     constexpr int TCOLS = 2 * NPOS;          // two 256-column accumulators
     constexpr int W_TILE = KT * 128;         // one filter tile (tap, channel block)
@@ -750,7 +760,7 @@ int ilog2(int v) {
 }
 
 template <int KT>
-constexpr int epi_total() { return EPI_WARPS * 32 * (KT / 4) * 2; }  // per-warp staging tiles
+constexpr int epi_total() { return epi_warps<KT>() * 32 * (KT / 4) * 2; }  // per-warp staging tiles
 
 // Largest band shift of the phase decomposition: i = (r*dh) div u over the
 // rows, j = (s*dw) div v over the columns.
@@ -889,7 +899,7 @@ gbconv_status_t launch_one(const TParams &prm, size_t smem, int grid, cudaStream
     });
     if (attr_err != cudaSuccess) return cuda_status(attr_err);
     return cuda_status(
-        launch_pdl(tc_fwd_t_kernel<KT, FP8, FUSED, OPH>, dim3(grid), dim3(NTHREADS), smem, st, prm));
+        launch_pdl(tc_fwd_t_kernel<KT, FP8, FUSED, OPH>, dim3(grid), dim3(nthreads<KT>()), smem, st, prm));
 }
 
 // forward launches (with or without the fused epilogue)
