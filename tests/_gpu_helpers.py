@@ -9,7 +9,17 @@ from paper_2207_00257_gb300 import binding as B
 from paper_2207_00257_gb300 import functional as F
 from paper_2207_00257_gb300.synth import ConvShape, make_inputs, sample_indices
 
-# tolerances (normalised error); see the design doc for their derivation
+# Tolerances on the error normalised by sum |x||w| (the workload's stated
+# bounds, and what the arithmetic allows):
+#   FP32: an FFMA chain of n terms errs by at most ~n * 2^-24 of sum|x||w| and
+#     typically ~sqrt(n) * 2^-24 (2e-6 at n = 1152), so 1e-5 holds with margin;
+#   BF16 output: rounding to BF16 costs at most 2^-9 of |y| <= sum|x||w|, plus
+#     ~1e-6 of FP32 accumulation; twice the rounding bound, 4e-3;
+#   BF16 / FP8 against the FP32 master values: input rounding (2^-9 per BF16
+#     operand, 2^-4 per E4M3 operand, averaging down over the sum) plus the
+#     output rounding, within the stated 1e-2 and 5e-2;
+#   FP32 output of BF16/E4M3 products: the products are exact in FP32, only
+#     the accumulation remains.
 TOL_F32 = 1e-5          # FP32 FFMA path vs FP64
 TOL_BF16_OUT = 4e-3     # BF16-rounded output vs oracle on the same (rounded) inputs
 TOL_BF16 = 1e-2         # BF16 path vs oracle on the FP32 master values
