@@ -277,7 +277,8 @@ def resnet_report(layers, res, pk, eb):
                     "frac_of_bf16_peak": round(tf / pk["bf16_tflops"], 4),
                     "frac_of_hbm": round(gbs / pk["hbm_gbs"], 4),
                     "frac_of_attainable": round(tf / attain, 4),
-                    "bound": "hbm" if ai * pk["hbm_gbs"] / 1e3 < pk["bf16_tflops"] else "tensor"})
+                    "bound": "hbm" if ai * pk["hbm_gbs"] / 1e3 < pk["bf16_tflops"] else "tensor",
+                    "algorithmic_bytes": by, "dram_bytes_ncu": ncu_traffic(sh.tag)})
     return out
 
 
