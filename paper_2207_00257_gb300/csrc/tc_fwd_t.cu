@@ -8,10 +8,12 @@
 //   D^T[k][e] = sum_{(r,s), c} W[k][(r,s)][c] * band[e + shift(r,s)][c]
 //
 // with M = KT output channels (64 or 128) and N = 256 extended output
-// positions per tcgen05.mma. On GB300 one MMA instruction costs about the
-// same for N = 64 and N = 128 and only grows from N = 128 to 256, so a layer
-// with 64 or 128 output channels runs 1.6-1.8x more tensor work per
-// instruction this way than with pixels on M.
+// positions per tcgen05.mma. With pixels on M a 64-channel layer issues
+// 128 x 64 x 16 MMAs, which sit on a ~27 ns per-instruction floor on GB300;
+// with channels on M it issues half as many 64 x 256 x 16 MMAs (M = 64 runs
+// at half the tensor rate), and a single thread issues every MMA of a CTA,
+// so fewer, larger instructions win: 1.5x end to end on a 3x3 64->64 layer
+// at 56x56, batch 32. With 128 channels the MMA is 128 x N at full rate.
 //
 //  * Strides by phase decomposition. Tap (r, s) of output (p, q) reads input
 //    row u*p - ph + r*dh = u*(p + i) + a - ph with a = (r*dh) mod u,
