@@ -311,6 +311,17 @@ def max_normalised_error(got, ref, bound) -> float:
     return float(np.max(np.abs(got - ref) / bound))
 
 
+# ---- the rectifier after a convolution (Sec. 5.B, backward pass) ----
+
+def relu_grad(y, g) -> np.ndarray:
+    """Gradient through y = max(z, 0) in float64: g where y > 0, else 0
+    (the derivative of the rectifier is 1 for z > 0 and 0 for z < 0; at
+    z = 0 the zero branch, as PyTorch's threshold backward takes it)."""
+    y = np.asarray(y, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    return np.where(y > 0, g, 0.0)
+
+
 # ---- negative log-likelihood loss (Sec. 5.B) ----
 
 NLL_REDUCTIONS = {"none": 0, "mean": 1, "sum": 2}

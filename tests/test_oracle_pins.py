@@ -11,7 +11,8 @@ fails at least one of them.
 * brute-force FFT cross-correlation agrees to 1e-12 on tiny inputs;
 * torch.nn.functional.conv2d in float64 (a library special case, test only);
 * adjoint identities <conv(x,w), g> = <x, dgrad(g,w)> = <w, wgrad(x,g)>;
-* central finite differences of L = sum g*y give dx, dw, db;
+* central finite differences of L = sum g*y give dx, dw, db, and through
+  a ReLU those of L = sum g*relu(y) (pre-activations kept off the kink);
 * the quantisers against their format definitions and torch's converters.
 """
 import itertools
@@ -251,6 +252,58 @@ def test_central_finite_differences(layout, st, pd, dl):
     assert np.max(np.abs(dx - dx_fd)) < 1e-9 * scale
     assert np.max(np.abs(dw - dw_fd)) < 1e-9 * scale
     assert np.max(np.abs(db - db_fd)) < 1e-9 * scale
+
+
+@pytest.mark.parametrize("layout", ["NCHW", "NHWC"])
+def test_relu_gradient_central_differences(layout):
+    """L = sum g * max(conv(x, w) + b, 0). With integer x, w and half-integer
+    b every pre-activation z is k + 1/2, at least 1/2 away from the kink, and
+    a step of 2^-10 in one element moves z by far less than that, so the
+    central difference sees one linear piece and is exact up to roundoff. The
+    chain rule through the oracle's relu_grad then gives dx, dw, db."""
+    p = Conv(1, 4, 6, 6, 4, 3, 3, (1, 1), (1, 1), (1, 1), layout)
+    r = _rng(18)
+    x = r.integers(-3, 4, size=p.x_shape).astype(np.float64)
+    w = r.integers(-3, 4, size=p.w_shape).astype(np.float64)
+    b = r.integers(-4, 4, size=4).astype(np.float64) + 0.5
+    g = r.normal(size=p.y_shape)
+    h = 2.0 ** -10
+    z = oracle.conv2d_fwd(p, x, w, b, nthreads=1)
+    assert np.min(np.abs(z)) >= 0.5 and np.any(z < 0) and np.any(z > 0)
+    y = oracle.conv2d_fwd(p, x, w, b, relu=True, nthreads=1)
+    assert np.array_equal(y, np.maximum(z, 0.0))
+
+    def L(xx, ww, bb):
+        return float(np.sum(oracle.conv2d_fwd(p, xx, ww, bb, relu=True, nthreads=1) * g))
+
+    def fd(arr):
+        out = np.empty(arr.size)
+        flat = arr.reshape(-1)
+        for i in range(arr.size):
+            keep = flat[i]
+            flat[i] = keep + h
+            lp = L(x, w, b)
+            flat[i] = keep - h
+            lm = L(x, w, b)
+            flat[i] = keep
+            out[i] = (lp - lm) / (2 * h)
+        return out.reshape(arr.shape)
+
+    gz = oracle.relu_grad(y, g)
+    # a plausible slip (the mask from z >= 0, or no mask) changes the result
+    assert not np.array_equal(gz, g)
+    scale = np.sum(np.abs(g)) * max(np.max(np.abs(x)), np.max(np.abs(w)), 1.0)
+    assert np.max(np.abs(oracle.conv2d_dgrad(p, gz, w) - fd(x))) < 1e-9 * scale
+    assert np.max(np.abs(oracle.conv2d_wgrad(p, x, gz) - fd(w))) < 1e-9 * scale
+    assert np.max(np.abs(oracle.conv2d_bgrad(p, gz) - fd(b))) < 1e-9 * scale
+
+
+def test_relu_gradient_at_the_kink_and_signs():
+    """Zero output (z <= 0) passes no gradient, positive output passes it
+    unchanged, whatever the sign of g; -0.0 counts as zero."""
+    y = np.array([0.0, -0.0, 1e-300, 2.5, -3.0, 0.0])
+    g = np.array([1.0, -2.0, 3.0, -4.0, 5.0, -6.0])
+    assert np.array_equal(oracle.relu_grad(y, g), np.array([0.0, 0.0, 3.0, -4.0, 0.0, 0.0]))
 
 
 @pytest.mark.parametrize("layout", ["NCHW", "NHWC"])
