@@ -4,7 +4,9 @@
 //   * 180-degree filter rotation with C and K exchanged (data gradient as a
 //     forward convolution),
 //   * FP8 E4M3 operand preparation: per-group scale max|v|/448 and RNE
-//     quantisation with saturation.
+//     quantisation with saturation,
+//   * the gradient through the ReLU that follows a convolution (the upstream
+//     gradient masked where the forward output is not positive).
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -359,6 +361,68 @@ __global__ void quant_kernel(const T *__restrict__ in, long long len,
     }
 }
 
+// Gradient through ReLU: out[i] = y[i] > 0 ? g[i] : 0, converted to the
+// output type (BF16 by round to nearest even). VEC: 8 elements per step with
+// 16-byte accesses (n % 8 == 0, every pointer 16-byte aligned).
+__device__ __forceinline__ void store8(float *p, const float (&v)[8]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4 *>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+}
+__device__ __forceinline__ void store8(__nv_bfloat16 *p, const float (&v)[8]) {
+    uint4 u;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    *reinterpret_cast<uint4 *>(p) = u;
+}
+template <typename TO>
+__device__ __forceinline__ TO from_f(float v);
+template <>
+__device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename TY, typename TG, typename TO, bool VEC>
+__global__ void relu_grad_kernel(const TY *__restrict__ y, const TG *g, TO *out, long long n) {
+    ptx::griddep_wait();
+    if (threadIdx.x == 0) ptx::griddep_launch();
+    const long long step = (long long)gridDim.x * blockDim.x;
+    if (VEC) {
+        for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 8; i < n; i += step * 8) {
+            float vy[8], vg[8];
+            load8(y + i, vy);
+            load8(g + i, vg);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) vg[k] = vy[k] > 0.f ? vg[k] : 0.f;
+            store8(out + i, vg);
+        }
+    } else {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += step)
+            out[i] = from_f<TO>(to_f(y[i]) > 0.f ? to_f(g[i]) : 0.f);
+    }
+}
+
+// FFMA issue-rate probe: 8 independent fused multiply-add chains per thread,
+// 16 steps each per loop trip (the multiplier and addend come from the caller,
+// so nothing folds). The result is written only if it equals a value no chain
+// reaches, which keeps every chain live.
+__global__ void __launch_bounds__(256) ffma_rate_kernel(long long iters, float m, float c,
+                                                        float *out) {
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = (float)(threadIdx.x + j) * 1e-3f;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) a[j] = fmaf(a[j], m, c);
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t += a[j];
+    if (t == -1.2345e30f) out[0] = t;
+}
+
 __global__ void finalize_scale(unsigned *__restrict__ amax_bits, long long rows) {
     ptx::griddep_wait();
     if (threadIdx.x == 0) ptx::griddep_launch();
@@ -515,6 +579,60 @@ gbconv_status_t launch_quantize_e4m3(const void *in, int in_dtype, long long row
     if (e == cudaSuccess)
         e = launch_pdl(finalize_scale, dim3(grid_for(rows, 256)), dim3(256), 0, st, amax, rows);
     return cuda_status(e);
+}
+
+
+gbconv_status_t launch_relu_grad(const void *y, int y_dtype, const void *g, int g_dtype, void *out,
+                                 int out_dtype, long long n, cudaStream_t st) {
+    if (n <= 0) return GBCONV_OK;
+    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const bool vec = n % 8 == 0 && al(y) && al(g) && al(out);
+    const unsigned grid = grid_for(vec ? n / 8 : n, 256);
+    cudaError_t e = cudaErrorInvalidValue;
+#define GBC_RG(TY, TG, TO)                                                                          \
+    e = vec ? launch_pdl(relu_grad_kernel<TY, TG, TO, true>, dim3(grid), dim3(256), 0, st,          \
+                         (const TY *)y, (const TG *)g, (TO *)out, n)                                \
+            : launch_pdl(relu_grad_kernel<TY, TG, TO, false>, dim3(grid), dim3(256), 0, st,         \
+                         (const TY *)y, (const TG *)g, (TO *)out, n)
+    const int code = (y_dtype == GBCONV_BF16) * 4 + (g_dtype == GBCONV_BF16) * 2 + (out_dtype == GBCONV_BF16);
+    switch (code) {
+        case 0: GBC_RG(float, float, float); break;
+        case 1: GBC_RG(float, float, __nv_bfloat16); break;
+        case 2: GBC_RG(float, __nv_bfloat16, float); break;
+        case 3: GBC_RG(float, __nv_bfloat16, __nv_bfloat16); break;
+        case 4: GBC_RG(__nv_bfloat16, float, float); break;
+        case 5: GBC_RG(__nv_bfloat16, float, __nv_bfloat16); break;
+        case 6: GBC_RG(__nv_bfloat16, __nv_bfloat16, float); break;
+        default: GBC_RG(__nv_bfloat16, __nv_bfloat16, __nv_bfloat16); break;
+    }
+#undef GBC_RG
+    return cuda_status(e);
+}
+
+
+gbconv_status_t measure_ffma_rate(long long iters, double *tflops, cudaStream_t st) {
+    const int blocks = sm_count() * 4, threads = 256;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return GBCONV_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return GBCONV_ERR_CUDA;
+    }
+    float *sink = nullptr;  // never written (see the kernel)
+    ffma_rate_kernel<<<blocks, threads, 0, st>>>(iters / 8 + 1, 0.9999999f, 1e-7f, sink);  // warm-up
+    cudaEventRecord(e0, st);
+    ffma_rate_kernel<<<blocks, threads, 0, st>>>(iters, 0.9999999f, 1e-7f, sink);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess || ms <= 0.f) return GBCONV_ERR_CUDA;
+    const double flops = 2.0 * 8 * 16 * (double)iters * blocks * threads;
+    *tflops = flops / (ms * 1e-3) / 1e12;
+    return GBCONV_OK;
 }
 
 }  // namespace gbc

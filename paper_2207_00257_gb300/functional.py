@@ -172,6 +172,21 @@ def conv2d_wgrad(x, dy, w_shape, stride=1, padding=0, dilation=1, layout="NHWC",
     return dw, db
 
 
+def relu_grad(y, g, out_dtype=None, out=None):
+    """Gradient through the ReLU of a forward with relu=True: g where y > 0,
+    else 0 (gbconv_relu_grad), in ``out_dtype`` (default: g's dtype)."""
+    _check_dev(y, g)
+    if y.numel() != g.numel():
+        raise ValueError("y and g must have the same number of elements")
+    od = out_dtype if out_dtype is not None else g.dtype
+    if out is None:
+        out = torch.empty(g.shape, dtype=od, device=g.device)
+    s = B.gbconv_relu_grad(y.data_ptr(), _DT[y.dtype], g.data_ptr(), _DT[g.dtype],
+                           out.data_ptr(), _DT[out.dtype], g.numel(), _stream())
+    B.check(s, "gbconv_relu_grad")
+    return out
+
+
 def quantize_e4m3(t, rows=1):
     """Per-group FP8 preparation: returns (codes as float8_e4m3fn, fp32 scales[rows])."""
     _check_dev(t)
@@ -223,8 +238,10 @@ class Conv2dFn(torch.autograd.Function):
         stride, padding, dilation, relu, layout, has_b, bdt = ctx.conf
         gy = gy.contiguous()
         if relu:
-            gy = gy * (y > 0).to(gy.dtype)  # derivative of max(., 0); mask only
-        gy = gy.to(x.dtype).contiguous()
+            # derivative of max(., 0) (and the cast to x's dtype) in the library
+            gy = relu_grad(y, gy, out_dtype=x.dtype)
+        else:
+            gy = gy.to(x.dtype).contiguous()
         dx = dw = db = None
         if ctx.needs_input_grad[0]:
             dx = conv2d_dgrad(gy, w, tuple(x.shape), stride, padding, dilation, layout,

@@ -11,7 +11,7 @@ from paper_2207_00257_gb300 import functional as F
 from paper_2207_00257_gb300.synth import (ConvShape, config_backward, config_backward_fd,
                                           make_inputs)
 
-from _gpu_helpers import TOL_ACC32, TOL_BF16_OUT, TOL_F32, f64, oconv, sampled
+from _gpu_helpers import TOL_ACC32, TOL_BF16_OUT, TOL_F32, f64, oconv
 
 pytestmark = pytest.mark.gpu
 
@@ -136,14 +136,138 @@ def test_backward_fd_size():
         assert max(e.values()) <= TOL_F32, e
 
 
-def test_backward_full_size_sampled():
-    """Backward workload: BF16 N=32, C=K=128, 56x56, 3x3 pad 1, g = N(0,1)."""
+def test_backward_full_size_every_output():
+    """Backward workload: BF16 N=32, C=K=128, 56x56, 3x3 pad 1, g = N(0,1).
+    Every element of dx (12.8 M), dw (147 456) and db against the oracle."""
     sh = config_backward()
-    nx = sh.N * sh.H * sh.W * sh.C
-    nw = sh.K * sh.R * sh.S * sh.C
-    e = _grads(sh, torch.bfloat16, seed=34, idx_dx=sampled(nx, 1000, 400),
-               idx_dw=sampled(nw, 300, 401))
+    e = _grads(sh, torch.bfloat16, seed=34)
     assert e["dx"] <= TOL_ACC32 and e["dw"] <= TOL_ACC32 and e["db"] <= TOL_ACC32, e
+
+
+def test_backward_full_size_bf16_dx_every_output():
+    """The same workload with dx in BF16 (the dtype autograd hands back)."""
+    sh = config_backward()
+    e = _grads(sh, torch.bfloat16, seed=35, out_dtype=torch.bfloat16)
+    assert e["dx"] <= TOL_BF16_OUT, e
+
+
+def test_strided_dgrad_full_size_every_output():
+    """Data gradient of the 3x3 stride-2 ResNet layer (128 -> 128, 56 -> 28,
+    batch 32) by sub-pixel phases: every element of dx."""
+    from paper_2207_00257_gb300.synth import resnet_layers
+    sh = resnet_layers(32)[3]
+    x, w, _, g = make_inputs(sh, 36, grad=True)
+    wg, gg = w.bfloat16(), g.bfloat16()
+    dx = F.conv2d_dgrad(gg.cuda(), wg.cuda(), tuple(x.shape), sh.stride, sh.pad, sh.dil, "NHWC",
+                        out_dtype=torch.float32)
+    F.device_error()
+    ref, bound = oracle.conv2d_dgrad(oconv(sh), f64(gg), f64(wg), with_bound=True)
+    err = oracle.max_normalised_error(f64(dx).reshape(-1), ref.reshape(-1), bound.reshape(-1))
+    assert err <= TOL_ACC32, err
+
+
+# ---- the gradient through ReLU (gbconv_relu_grad) ----
+
+_DTS = (torch.float32, torch.bfloat16)
+
+
+@pytest.mark.parametrize("yd", _DTS, ids=["yf32", "ybf16"])
+@pytest.mark.parametrize("gd", _DTS, ids=["gf32", "gbf16"])
+@pytest.mark.parametrize("od", _DTS, ids=["of32", "obf16"])
+@pytest.mark.parametrize("n", [1, 7, 8, 4099, 300000])
+def test_relu_grad_kernel_bitwise(yd, gd, od, n):
+    """g_out = g where y > 0 else 0, bit for bit the oracle's definition
+    (then rounded to BF16 by the oracle's quantiser for BF16 outputs). y holds
+    exact zeros (ReLU outputs), negative values and -0.0."""
+    gen = torch.Generator().manual_seed(90 + n)
+    y = torch.randn(n, generator=gen).clamp_min(0.0)
+    y[1::7] = -torch.rand(len(range(1, n, 7)), generator=gen)
+    if n > 3:
+        y[3] = -0.0
+    g = torch.randn(n, generator=gen) * 3
+    yy, gg = y.to(yd), g.to(gd)
+    out = F.relu_grad(yy.cuda(), gg.cuda(), out_dtype=od)
+    F.device_error()
+    ref = oracle.relu_grad(f64(yy), f64(gg))
+    if od == torch.bfloat16:
+        ref = oracle.round_bf16(ref)
+    else:
+        ref = ref.astype(np.float32).astype(np.float64)
+    assert np.array_equal(f64(out), ref)
+
+
+def test_relu_grad_in_place_and_unaligned():
+    """In place (g_out = g), and views one element off the 16-byte boundary
+    (the scalar path)."""
+    gen = torch.Generator().manual_seed(95)
+    n = 10001
+    y = torch.randn(n + 1, generator=gen).bfloat16().cuda()
+    g = torch.randn(n + 1, generator=gen).bfloat16().cuda()
+    ref = oracle.relu_grad(f64(y), f64(g))
+    g2 = g.clone()
+    F.relu_grad(y, g2, out=g2)
+    F.device_error()
+    assert np.array_equal(f64(g2), ref)
+    out = torch.empty(n + 1, dtype=torch.float32, device="cuda")
+    F.relu_grad(y[1:], g[1:], out_dtype=torch.float32, out=out[1:])
+    F.device_error()
+    assert np.array_equal(f64(out[1:]), ref[1:])
+
+
+def test_relu_grad_rejects_overlap():
+    y = torch.zeros(64, dtype=torch.bfloat16, device="cuda")
+    g = torch.zeros(64, dtype=torch.bfloat16, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    s = B.gbconv_relu_grad(y.data_ptr(), B.GBCONV_BF16, g.data_ptr(), B.GBCONV_BF16,
+                           y.data_ptr(), B.GBCONV_BF16, 64, st)
+    assert s == B.GBCONV_ERR_INVALID_ARG
+    s = B.gbconv_relu_grad(y.data_ptr(), B.GBCONV_BF16, g.data_ptr(), B.GBCONV_BF16,
+                           g.data_ptr() + 2, B.GBCONV_BF16, 32, st)
+    assert s == B.GBCONV_ERR_INVALID_ARG
+    assert B.gbconv_relu_grad(y.data_ptr(), B.GBCONV_E4M3, g.data_ptr(), B.GBCONV_BF16,
+                              g.data_ptr(), B.GBCONV_BF16, 64, st) == B.GBCONV_ERR_UNSUPPORTED
+
+
+def _relu_case(sh, dtype, seed):
+    """Integer x, w and half-integer b: every pre-activation z is k + 1/2, so
+    the ReLU mask (z > 0) is the same on both sides whatever the rounding."""
+    gen = torch.Generator().manual_seed(seed)
+    x = torch.randint(-3, 4, sh.x_shape(), generator=gen).float()
+    w = torch.randint(-3, 4, sh.w_shape(), generator=gen).float()
+    b = torch.randint(-4, 4, (sh.K,), generator=gen).float() + 0.5
+    g = torch.randn(sh.y_shape(), generator=gen)
+    dev = "cuda"
+    xg = x.to(dtype).to(dev).requires_grad_()
+    wg = w.to(dtype).to(dev).requires_grad_()
+    bg = b.to(dev).requires_grad_()
+    y = F.conv2d_autograd(xg, wg, bg, sh.stride, sh.pad, sh.dil, True, sh.layout)
+    gd = g.to(y.dtype)
+    y.backward(gd.to(dev))
+    F.device_error()
+    p = oconv(sh)
+    z = oracle.conv2d_fwd(p, f64(x), f64(w), f64(b))
+    assert np.min(np.abs(z)) >= 0.5 and np.any(z < 0) and np.any(z > 0)
+    gz = oracle.relu_grad(np.maximum(z, 0.0), f64(gd))
+    dxr, dxb = oracle.conv2d_dgrad(p, gz, f64(w), with_bound=True)
+    dwr, dwb = oracle.conv2d_wgrad(p, f64(x), gz, with_bound=True)
+    dbr, dbb = oracle.conv2d_bgrad(p, gz, with_bound=True)
+    return (oracle.max_normalised_error(f64(xg.grad), dxr, dxb),
+            oracle.max_normalised_error(f64(wg.grad), dwr, dwb),
+            oracle.max_normalised_error(f64(bg.grad), dbr, dbb))
+
+
+def test_autograd_relu_bf16_matches_oracle():
+    """relu=True through Conv2dFn: the library masks the upstream gradient
+    (gbconv_relu_grad) and runs dgrad / wgrad; against the oracle's analytic
+    gradient of sum g * relu(conv(x, w) + b)."""
+    ex, ew, eb = _relu_case(ConvShape(2, 32, 10, 10, 64, 3, 3, 1, 1, 1), torch.bfloat16, 39)
+    # dx and dw come back in BF16 (rounding 2^-9), db in fp32
+    assert ex <= TOL_BF16_OUT and ew <= TOL_BF16_OUT and eb <= TOL_ACC32, (ex, ew, eb)
+
+
+def test_autograd_relu_fp32_nchw_strided_matches_oracle():
+    ex, ew, eb = _relu_case(ConvShape(2, 6, 9, 8, 5, 3, 3, 2, 1, 1, "NCHW"), torch.float32, 40)
+    assert ex <= TOL_F32 and ew <= TOL_F32 and eb <= TOL_F32, (ex, ew, eb)
 
 
 def test_wgrad_deterministic():

@@ -31,12 +31,14 @@ def _inputs(shapes, seed0):
     return xs, ws, bs, masters
 
 
-def _check(shapes, xs, ws, bs, masters, ys, relu, max_points=None):
+def _check(shapes, xs, ws, bs, masters, ys, relu, max_points=None, full_below_flops=0):
+    """Every output of problems under `full_below_flops`, else `max_points`
+    seeded samples (every output when max_points is None)."""
     for i, sh in enumerate(shapes):
         p = oconv(sh)
         idx = None
         total = int(np.prod(sh.y_shape()))
-        if max_points is not None and total > max_points:
+        if max_points is not None and total > max_points and sh.flops >= full_below_flops:
             idx = sampled(total, max_points, seed=500 + i)
         got = f64(ys[i]).reshape(-1)
         if idx is not None:
@@ -92,8 +94,9 @@ def test_grouped_matches_single_launches_bitwise():
 
 def test_grouped_workload_64_problems_graph():
     """The 64-problem workload (shapes drawn from seed 1, committed JSON), one
-    persistent launch captured in a CUDA graph and replayed; sampled outputs
-    of every problem against the oracle."""
+    persistent launch captured in a CUDA graph and replayed; every output of
+    each problem under 1 GFLOP and 4096 seeded outputs of the larger ones
+    against the oracle."""
     shapes = grouped_problems()
     assert len(shapes) == 64
     xs, ws, bs, masters = _inputs(shapes, 1000)
@@ -112,4 +115,4 @@ def test_grouped_workload_64_problems_graph():
     graph.replay()
     torch.cuda.synchronize()
     F.device_error()
-    _check(shapes, xs, ws, bs, masters, ys, relu=True, max_points=300)
+    _check(shapes, xs, ws, bs, masters, ys, relu=True, max_points=4096, full_below_flops=1e9)

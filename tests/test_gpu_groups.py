@@ -9,7 +9,7 @@ import oracle
 from paper_2207_00257_gb300 import binding as B
 from paper_2207_00257_gb300 import functional as F
 
-from _gpu_helpers import TOL_ACC32, TOL_BF16_OUT, TOL_F32, f64, sampled
+from _gpu_helpers import TOL_ACC32, TOL_BF16_OUT, TOL_F32, f64
 
 pytestmark = pytest.mark.gpu
 
@@ -128,7 +128,7 @@ FULL_SIZE = [(32, 128, 56, 128), (32, 128, 56, 32), (8, 256, 56, 256)]
 
 
 @pytest.mark.parametrize("N,C,HW,G", FULL_SIZE, ids=lambda v: str(v))
-def test_groups_full_size_sampled(N, C, HW, G):
+def test_groups_full_size_every_output(N, C, HW, G):
     p = oracle.Conv(N, C, HW, HW, C, 3, 3, 1, 1, 1, "NHWC", groups=G)
     g = torch.Generator().manual_seed(96)
     x = torch.randn(p.x_shape, generator=g).bfloat16()
@@ -136,9 +136,8 @@ def test_groups_full_size_sampled(N, C, HW, G):
     b = torch.rand(C, generator=g) * 0.2 - 0.1
     y = F.conv2d(x.cuda(), w.cuda(), b.cuda(), 1, 1, 1, True, groups=G)
     F.device_error()
-    idx = sampled(int(np.prod(p.y_shape)), 8000, seed=97)
-    ref, bound = oracle.conv2d_fwd(p, f64(x), f64(w), f64(b), True, idx=idx, with_bound=True)
-    err = oracle.max_normalised_error(f64(y).reshape(-1)[idx], ref.reshape(-1), bound.reshape(-1))
+    ref, bound = oracle.conv2d_fwd(p, f64(x), f64(w), f64(b), True, with_bound=True)
+    err = oracle.max_normalised_error(f64(y).reshape(-1), ref.reshape(-1), bound.reshape(-1))
     assert err <= TOL_BF16_OUT, err
 
 

@@ -3,10 +3,11 @@ device memory or pass a workspace (a framework allocator that must own every
 device byte, a fixed memory budget, work enqueued where an allocation would
 stall or be refused). Its scratch is a static device array inside the library.
 
-Checked through the C ABI against conv2d_dgrad (which takes a workspace) on
-two calls in a row with different filters, so that a second call cannot pass
-on scratch left behind by the first. This file is collected last; it passes
-on its own in a fresh process and after the rest of the suite."""
+Checked through the C ABI against the FP64 oracle's data gradient and against
+conv2d_dgrad (which takes a workspace), on two calls in a row with different
+filters, so that a second call cannot pass on scratch left behind by the
+first. This file is collected last; it passes on its own in a fresh process
+and after the rest of the suite."""
 import numpy as np
 import pytest
 import torch
@@ -40,10 +41,13 @@ def _with_workspace(prob, dy, w, dx):
                            nbytes, st), "conv2d_dgrad")
 
 
-@pytest.mark.parametrize("sh", [ConvShape(2, 64, 9, 11, 96, 3, 3, 1, 1, 1),     # tensor cores
-                                ConvShape(2, 32, 11, 11, 32, 3, 3, 2, 1, 1)],   # CUDA cores
-                         ids=["stride1-static-scratch", "stride2-no-scratch"])
-def test_noalloc_matches_workspace_dgrad_two_calls(sh):
+@pytest.mark.parametrize("sh", [ConvShape(2, 64, 9, 11, 96, 3, 3, 1, 1, 1),     # rotated filter
+                                ConvShape(2, 32, 11, 11, 32, 3, 3, 2, 1, 1),    # sub-pixel phases
+                                ConvShape(1, 64, 23, 19, 96, 5, 5, 2, 2, 1),    # phases, 5x5
+                                ConvShape(2, 12, 11, 11, 20, 3, 3, 2, 1, 1)],   # CUDA cores
+                         ids=["stride1-static-scratch", "stride2-static-scratch",
+                              "stride2-5x5-static-scratch", "channels12-no-scratch"])
+def test_noalloc_matches_oracle_and_workspace_dgrad_two_calls(sh):
     st = torch.cuda.current_stream().cuda_stream
     prob = _prob(sh, B.GBCONV_F32)
     p = oconv(sh)
@@ -56,11 +60,15 @@ def test_noalloc_matches_workspace_dgrad_two_calls(sh):
                 "conv2d_dgrad_noalloc")
         _with_workspace(prob, gb, wb, dx_ref)
         B.check(B.gbconv_get_device_error(st), "device")
-        # tolerance normaliser: sum |g||w| over each output's terms (the oracle's bound)
-        _, bound = oracle.conv2d_dgrad(p, f64(gb), f64(wb), with_bound=True)
+        assert not torch.isnan(dx_new).any()
+        # the oracle's data gradient on the same BF16 operands; the tolerance is
+        # normalised by sum |g||w| over each output's terms
+        ref, bound = oracle.conv2d_dgrad(p, f64(gb), f64(wb), with_bound=True)
+        err = oracle.max_normalised_error(f64(dx_new), ref, bound)
+        assert err <= TOL_ACC32, (call, err)
+        # and the entry point that takes a workspace
         err = oracle.max_normalised_error(f64(dx_new), f64(dx_ref), bound)
         assert err <= TOL_ACC32, (call, err)
-        assert not torch.isnan(dx_new).any()
 
 
 def test_noalloc_refuses_filters_beyond_the_static_scratch():
