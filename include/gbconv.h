@@ -109,11 +109,21 @@ typedef struct {
  * GBCONV_ALGO_SHIFT (stride 1 only: one input band per channel block, filter
  * taps as row shifts of it) or GBCONV_ALGO_SHIFT_T (the same band with the
  * GEMM transposed: output channels on the MMA's M, 256 positions on N; stride
- * 1 and K <= 128 only). A zero field means "library default". */
+ * 1 and K <= 128 only), GBCONV_ALGO_SIMT (the CUDA-core FFMA kernel, for
+ * F32 and BF16 inputs; a reference point for the tensor-core paths),
+ * GBCONV_ALGO_PBAND (BF16 multi-tap layers with K <= 128, strides up to 4:
+ * output pixels on the MMA's M, one input band per stride phase and channel
+ * block, the filter resident in shared memory, one SM per 128-position tile)
+ * or GBCONV_ALGO_PBAND_PAIR (the same on pairs of SMs: one 256-row MMA per
+ * pair, each SM holding half of the filter). A zero field means "library
+ * default". */
 #define GBCONV_ALGO_AUTO 0
 #define GBCONV_ALGO_IM2COL 1
 #define GBCONV_ALGO_SHIFT 2
 #define GBCONV_ALGO_SHIFT_T 3
+#define GBCONV_ALGO_SIMT 4
+#define GBCONV_ALGO_PBAND 5
+#define GBCONV_ALGO_PBAND_PAIR 6
 typedef struct {
     int32_t block_n;
     int32_t stages;
@@ -256,6 +266,21 @@ gbconv_status_t conv2d_grouped(int32_t count, const gbconv_problem_t *probs,
                                const float *const *bias, void *const *y, void *ws,
                                size_t ws_bytes, gbconv_stream_t stream);
 
+/* Gradient through the ReLU of a forward run with GBCONV_FLAG_RELU (paper
+ * Sec. 5.B, backward pass: every ResNet-50 convolution is followed by a
+ * rectifier, whose derivative masks the upstream gradient):
+ *   g_out[i] = y[i] > 0 ? g[i] : 0      for 0 <= i < n
+ * y is the forward's output (y = max(z, 0), so y > 0 exactly where z > 0),
+ * g the upstream gradient of y, g_out the gradient of z, ready for
+ * conv2d_dgrad / conv2d_wgrad. Element types y_dtype, g_dtype, out_dtype are
+ * GBCONV_F32 or GBCONV_BF16 each (else GBCONV_ERR_UNSUPPORTED); a BF16 output
+ * is rounded to nearest even. All three are device pointers to n elements in
+ * any common layout. g_out may be g itself (same dtype; in place) but must not
+ * overlap y or partly overlap g (GBCONV_ERR_INVALID_ARG). n = 0 does nothing.
+ * Asynchronous on stream; no workspace. */
+gbconv_status_t gbconv_relu_grad(const void *y, int32_t y_dtype, const void *g, int32_t g_dtype,
+                                 void *g_out, int32_t out_dtype, int64_t n, gbconv_stream_t stream);
+
 /* FP8 operand preparation for the E4M3 forward path. `in` holds `rows`
  * contiguous groups of `len` values (in_dtype F32 or BF16). Per group,
  * entirely in binary32:
@@ -309,14 +334,14 @@ gbconv_status_t gbconv_debug_set(int32_t key, int64_t value);
  * variant of conv2d_dgrad, not part of the method.
  *
  * Same arguments, layouts and results as conv2d_dgrad minus the workspace.
- * Where conv2d_dgrad would place the rotated filter in the caller's workspace
- * (BF16 NHWC, stride 1), this entry point uses a static device array of
+ * Where conv2d_dgrad would place the rotated filter (BF16 NHWC, stride 1) or
+ * the transposed filter (the sub-pixel phases of strided BF16 NHWC layers) in
+ * the caller's workspace, this entry point uses a static device array of
  * GBCONV_DGRAD_STATIC_SCRATCH_BYTES bytes that the library holds on every GPU
  * that loads it, until the process exits. Filters whose K*R*S*C*2 bytes exceed
  * that size are refused with GBCONV_ERR_WORKSPACE before anything is enqueued.
- * Every other problem (including the strided layers that conv2d_dgrad runs
- * as sub-pixel phases) runs here on the CUDA-core kernel and needs no
- * scratch at all.
+ * Every other problem runs here on the CUDA-core kernel and needs no scratch
+ * at all (as does a problem whose stored config asks for GBCONV_ALGO_SIMT).
  *
  * The first call on each device looks up the array's device address (a CUDA
  * runtime query, done once per device with that device current); make that
@@ -327,6 +352,16 @@ gbconv_status_t gbconv_debug_set(int32_t key, int64_t value);
 #define GBCONV_DGRAD_STATIC_SCRATCH_BYTES (8u * 1024u * 1024u)
 gbconv_status_t conv2d_dgrad_noalloc(const gbconv_problem_t *prob, const void *dy,
                                      const void *w, void *dx, gbconv_stream_t stream);
+
+/* Measured FP32 CUDA-core throughput of the current device, the roofline
+ * denominator of the plain FP32 kernel (its nominal value is 2 x 128 FFMA
+ * lanes x SMs x clock). Runs a probe kernel of fused multiply-adds (8
+ * independent chains per thread, 4 blocks of 256 threads per SM, `iters`
+ * trips of 128 FFMAs per thread) on `stream`, times it with CUDA events,
+ * synchronises and writes TFLOP/s (2 flops per FFMA) to *tflops (host
+ * pointer). Not for the hot path; the paper has no counterpart (it is part of
+ * the measurement, not of the method). GBCONV_ERR_INVALID_ARG for iters < 1. */
+gbconv_status_t gbconv_measure_ffma_tflops(int64_t iters, double *tflops, gbconv_stream_t stream);
 
 /* Library version, as major*10000 + minor*100 + patch. */
 int32_t gbconv_version(void);

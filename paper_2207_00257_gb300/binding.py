@@ -27,6 +27,8 @@ GBCONV_OP_FWD, GBCONV_OP_DGRAD, GBCONV_OP_WGRAD = 0, 1, 2
 GBCONV_FLAG_BIAS, GBCONV_FLAG_RELU = 1, 2
 GBCONV_DEBUG_WAIT_LIMIT_NS, GBCONV_DEBUG_SKIP_LOADS = 1, 2
 GBCONV_ALGO_AUTO, GBCONV_ALGO_IM2COL, GBCONV_ALGO_SHIFT, GBCONV_ALGO_SHIFT_T = 0, 1, 2, 3
+GBCONV_ALGO_SIMT = 4
+GBCONV_ALGO_PBAND, GBCONV_ALGO_PBAND_PAIR = 5, 6
 
 # every symbol include/gbconv.h declares
 EXPORTS = [
@@ -36,6 +38,7 @@ EXPORTS = [
     "gbconv_get_device_error", "gbconv_status_string", "gbconv_debug_set", "gbconv_version",
     "gbconv_shutdown", "conv2d_dgrad_noalloc", "conv2d_fwd_fused", "gbconv_bn_fold",
     "gbconv_nll_workspace_size", "gbconv_nll_loss_fwd", "gbconv_nll_loss_bwd",
+    "gbconv_relu_grad", "gbconv_measure_ffma_tflops",
 ]
 
 
@@ -94,6 +97,10 @@ _SIGS = {
                                         ctypes.c_size_t, _P]),
     "gbconv_bn_fold": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, ctypes.c_float, _P, _P, _P,
                                       _P]),
+    "gbconv_relu_grad": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32,
+                                        ctypes.c_int64, _P]),
+    "gbconv_measure_ffma_tflops": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                                  _P]),
     "gbconv_nll_workspace_size": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
     "gbconv_nll_loss_fwd": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int64,
                                            ctypes.c_int64, ctypes.c_int32, _P, _P, _P,
@@ -225,6 +232,11 @@ def gbconv_quantize_e4m3(inp, in_dtype, rows, length, out, scale, stream):
                                       _vp(stream))
 
 
+def gbconv_relu_grad(y, y_dtype, g, g_dtype, g_out, out_dtype, n, stream):
+    return lib().gbconv_relu_grad(_vp(y), y_dtype, _vp(g), g_dtype, _vp(g_out), out_dtype, n,
+                                  _vp(stream))
+
+
 def gbconv_get_config(op, prob):
     c = gbconv_config_t()
     s = lib().gbconv_get_config(op, ctypes.byref(prob), ctypes.byref(c))
@@ -260,6 +272,12 @@ def gbconv_status_string(status):
 
 def gbconv_debug_set(key, value):
     return lib().gbconv_debug_set(key, value)
+
+
+def gbconv_measure_ffma_tflops(iters, stream):
+    v = ctypes.c_double(0.0)
+    s = lib().gbconv_measure_ffma_tflops(iters, ctypes.byref(v), _vp(stream))
+    return s, v.value
 
 
 def gbconv_version():

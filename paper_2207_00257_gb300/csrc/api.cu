@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -22,11 +23,51 @@ __device__ unsigned int g_gbconv_error_word;
 static __device__ __align__(256) unsigned char g_dgrad_static_scratch[GBCONV_DGRAD_STATIC_SCRATCH_BYTES];
 
 namespace gbc {
+// Reads a tuning-table JSON file into the table (defined below the C ABI).
+gbconv_status_t load_cache_file(const char *path);
+
 namespace {
 
 std::mutex g_mu;
-uint64_t g_wait_ns = 2000000000ull;
 int g_skip_loads = 0;
+
+// Environment settings, read once:
+//   GBCONV_WAIT_LIMIT  default time limit of every in-kernel wait, in ns
+//                      (default 2e9);
+//   GBCONV_TUNE_CACHE  path of a tuning-table JSON file: loaded on the first
+//                      lookup, rewritten after every gbconv_tune;
+//   GBCONV_LOG         0 (default) silent, 1 failed calls, 2 every call's
+//                      problem and configuration, on stderr.
+uint64_t env_u64(const char *name, uint64_t dflt) {
+    const char *v = getenv(name);
+    if (!v || !*v) return dflt;
+    char *end = nullptr;
+    unsigned long long x = strtoull(v, &end, 10);
+    return (end && *end == 0 && x > 0) ? (uint64_t)x : dflt;
+}
+uint64_t default_wait_ns() {
+    static const uint64_t v = env_u64("GBCONV_WAIT_LIMIT", 2000000000ull);
+    return v;
+}
+int log_level() {
+    static const int v = (int)env_u64("GBCONV_LOG", 0);
+    return v;
+}
+uint64_t g_wait_ns = default_wait_ns();
+
+void log_call(const char *what, const gbconv_problem_t *p, const TcConfig *c, gbconv_status_t st) {
+    const int lv = log_level();
+    if (lv <= 0 || (lv == 1 && st == GBCONV_OK) || !p) return;
+    fprintf(stderr,
+            "[gbconv] %s N=%d C=%d H=%d W=%d K=%d R=%d S=%d stride=%d,%d pad=%d,%d dil=%d,%d "
+            "in=%d out=%d layout=%d flags=%u groups=%d",
+            what, p->N, p->C, p->H, p->W, p->K, p->R, p->S, p->stride_h, p->stride_w, p->pad_h,
+            p->pad_w, p->dil_h, p->dil_w, p->in_dtype, p->out_dtype, p->layout, p->flags, p->groups);
+    if (c)
+        fprintf(stderr, " block_n=%d stages=%d split_k=%d raster=%d algo=%d", c->block_n, c->stages,
+                c->split_k, c->raster, c->algo);
+    fprintf(stderr, " -> %d\n", (int)st);
+}
 
 struct DevInfo {
     unsigned int *err = nullptr;
@@ -71,7 +112,23 @@ std::string problem_key(int op, const gbconv_problem_t &p) {
     return buf;
 }
 
+void load_env_cache_once() {
+    static std::once_flag once;
+    std::call_once(once, []() {
+        const char *path = getenv("GBCONV_TUNE_CACHE");
+        if (path && *path) {
+            FILE *f = fopen(path, "r");
+            if (f) {
+                fclose(f);
+                if (load_cache_file(path) != GBCONV_OK && log_level() > 0)
+                    fprintf(stderr, "[gbconv] could not parse GBCONV_TUNE_CACHE=%s\n", path);
+            }
+        }
+    });
+}
+
 bool tuned(int op, const gbconv_problem_t &p, TcConfig *out) {
+    load_env_cache_once();
     std::string k = problem_key(op, p);
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_tune.find(k);
@@ -299,6 +356,10 @@ gbconv_status_t do_fwd(const Dims &d, const TcConfig &cfg, const void *x, const 
         if (d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
         return launch_simt_fwd(d, x, w, bias, y, st, fz);
     }
+    if (cfg.algo == GBCONV_ALGO_SIMT) {  // the CUDA-core kernel on request (BF16 in)
+        if (d.in_dtype != GBCONV_BF16) return GBCONV_ERR_UNSUPPORTED;
+        return launch_simt_fwd(d, x, w, bias, y, st, fz);
+    }
     if (d.layout != GBCONV_NHWC) return GBCONV_ERR_UNSUPPORTED;
     if (d.in_dtype == GBCONV_E4M3 && (!x_scale || !w_scale)) return GBCONV_ERR_INVALID_ARG;
     gbconv_status_t s = check_tc_fwd(d, x, w, y);
@@ -312,6 +373,7 @@ gbconv_status_t do_dgrad(const Dims &d, const TcConfig &cfg, const void *dy, con
     if ((long long)d.N * d.H * d.W == 0) return GBCONV_OK;
     if (d.in_dtype == GBCONV_E4M3 || d.out_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
     if (d.in_dtype == GBCONV_F32 && d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
+    if (cfg.algo == GBCONV_ALGO_SIMT) return launch_simt_dgrad(d, dy, w, dx, st);
     Dims t;
     if (dgrad_as_fwd(d, &t)) {
         size_t need = round256((size_t)d.K * d.R * d.S * d.C * 2);
@@ -434,11 +496,16 @@ gbconv_status_t conv2d_fwd(const gbconv_problem_t *prob, const void *x, const vo
     if (d.N == 0) return GBCONV_OK;  // empty batch: nothing to read or write
     if (!x || !w || !y || ((d.flags & GBCONV_FLAG_BIAS) && !bias)) return GBCONV_ERR_INVALID_ARG;
     if (x == y || w == y) return GBCONV_ERR_INVALID_ARG;
-    if (nchw_bf16(d))
-        return do_fwd_nchw_bf16(d, x, w, bias, y, ws, ws_bytes, static_cast<cudaStream_t>(stream),
-                                Fused{});
-    return do_fwd(d, config_for(GBCONV_OP_FWD, *prob, d), x, w, bias, x_scale, w_scale, y,
-                  static_cast<cudaStream_t>(stream));
+    if (nchw_bf16(d)) {
+        s = do_fwd_nchw_bf16(d, x, w, bias, y, ws, ws_bytes, static_cast<cudaStream_t>(stream),
+                             Fused{});
+        log_call("conv2d_fwd", prob, nullptr, s);
+        return s;
+    }
+    const TcConfig c = config_for(GBCONV_OP_FWD, *prob, d);
+    s = do_fwd(d, c, x, w, bias, x_scale, w_scale, y, static_cast<cudaStream_t>(stream));
+    log_call("conv2d_fwd", prob, &c, s);
+    return s;
 }
 
 gbconv_status_t conv2d_fwd_fused(const gbconv_problem_t *prob, const void *x, const void *w,
@@ -513,8 +580,10 @@ gbconv_status_t conv2d_dgrad(const gbconv_problem_t *prob, const void *dy, const
     if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;
     if (d.N == 0) return GBCONV_OK;  // empty batch: dx is empty
     if (!dy || !w || !dx || dx == dy || dx == w) return GBCONV_ERR_INVALID_ARG;
-    return do_dgrad(d, config_for(GBCONV_OP_DGRAD, *prob, d), dy, w, dx, ws, ws_bytes,
-                    static_cast<cudaStream_t>(stream));
+    const TcConfig c = config_for(GBCONV_OP_DGRAD, *prob, d);
+    s = do_dgrad(d, c, dy, w, dx, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+    log_call("conv2d_dgrad", prob, &c, s);
+    return s;
 }
 
 gbconv_status_t conv2d_wgrad(const gbconv_problem_t *prob, const void *x, const void *dy,
@@ -525,8 +594,10 @@ gbconv_status_t conv2d_wgrad(const gbconv_problem_t *prob, const void *x, const 
     if (s != GBCONV_OK) return s;
     if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;
     if (!dw || (d.N > 0 && (!x || !dy))) return GBCONV_ERR_INVALID_ARG;
-    return do_wgrad(d, config_for(GBCONV_OP_WGRAD, *prob, d), x, dy, dw, db, ws, ws_bytes,
-                    static_cast<cudaStream_t>(stream));
+    const TcConfig c = config_for(GBCONV_OP_WGRAD, *prob, d);
+    s = do_wgrad(d, c, x, dy, dw, db, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+    log_call("conv2d_wgrad", prob, &c, s);
+    return s;
 }
 
 gbconv_status_t conv2d_grouped(int32_t count, const gbconv_problem_t *probs, const void *const *x,
@@ -556,6 +627,28 @@ gbconv_status_t conv2d_grouped(int32_t count, const gbconv_problem_t *probs, con
     if (make_guard().err == nullptr) return GBCONV_ERR_CUDA;
     return launch_tc_grouped(count, d.data(), cfg.data(), x, w, b.data(), y,
                              static_cast<cudaStream_t>(stream));
+}
+
+gbconv_status_t gbconv_relu_grad(const void *y, int32_t y_dtype, const void *g, int32_t g_dtype,
+                                 void *g_out, int32_t out_dtype, int64_t n, gbconv_stream_t stream) {
+    if (n < 0) return GBCONV_ERR_INVALID_ARG;
+    if (n == 0) return GBCONV_OK;
+    if (!y || !g || !g_out) return GBCONV_ERR_INVALID_ARG;
+    auto ok = [](int32_t t) { return t == GBCONV_F32 || t == GBCONV_BF16; };
+    if (!ok(y_dtype) || !ok(g_dtype) || !ok(out_dtype)) return GBCONV_ERR_UNSUPPORTED;
+    const int eo = out_dtype == GBCONV_F32 ? 4 : 2;
+    const int eg = g_dtype == GBCONV_F32 ? 4 : 2;
+    const int ey = y_dtype == GBCONV_F32 ? 4 : 2;
+    // g_out may be g itself (same element type, same start) but must not
+    // partly overlap g or overlap y at all
+    auto overlap = [n](const void *a, int ea, const void *b, int eb) {
+        const char *pa = static_cast<const char *>(a), *pb = static_cast<const char *>(b);
+        return pa < pb + n * eb && pb < pa + n * ea;
+    };
+    if (overlap(g_out, eo, y, ey)) return GBCONV_ERR_INVALID_ARG;
+    if (overlap(g_out, eo, g, eg) && !(g_out == g && eo == eg)) return GBCONV_ERR_INVALID_ARG;
+    return launch_relu_grad(y, y_dtype, g, g_dtype, g_out, out_dtype, n,
+                            static_cast<cudaStream_t>(stream));
 }
 
 gbconv_status_t gbconv_quantize_e4m3(const void *in, int32_t in_dtype, int64_t rows, int64_t len,
@@ -590,7 +683,7 @@ gbconv_status_t gbconv_set_config(int32_t op, const gbconv_problem_t *prob,
         cfg->block_n != 256)
         return GBCONV_ERR_INVALID_ARG;
     if (cfg->split_k < 0 || cfg->split_k > 1024 || cfg->stages < 0 || cfg->raster < 0 ||
-        cfg->raster > 1 || cfg->algo < GBCONV_ALGO_AUTO || cfg->algo > GBCONV_ALGO_SHIFT_T)
+        cfg->raster > 1 || cfg->algo < GBCONV_ALGO_AUTO || cfg->algo > GBCONV_ALGO_PBAND_PAIR)
         return GBCONV_ERR_INVALID_ARG;
     TcConfig c = config_for(op, *prob, d);  // defaults for zero fields
     if (cfg->block_n) c.block_n = cfg->block_n;
@@ -624,24 +717,46 @@ gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void
         }
     } else {
         Dims t = d;
-        bool tc = op == GBCONV_OP_FWD ? tc_fwd_supported(d) : dgrad_as_fwd(d, &t);
+        const bool fwd_tc = op == GBCONV_OP_FWD && tc_fwd_supported(d);
+        const bool rotated = op == GBCONV_OP_DGRAD && dgrad_as_fwd(d, &t);
+        const bool phases = op == GBCONV_OP_DGRAD && !rotated && tc_dgrad_t_supported(d);
         const int kout = op == GBCONV_OP_FWD ? d.K : d.C;
-        if (tc) {
+        if (fwd_tc || rotated) {
             for (int bn : {32, 64, 128, 256}) {
                 if (bn > 32 && bn / 2 >= kout) continue;  // wider than needed
                 for (int algo : {GBCONV_ALGO_IM2COL, GBCONV_ALGO_SHIFT, GBCONV_ALGO_SHIFT_T}) {
                     if (algo == GBCONV_ALGO_SHIFT && !tc_fwd_shift_supported(t, bn)) continue;
                     // the transposed kernel picks its own tile: try it once
                     if (algo == GBCONV_ALGO_SHIFT_T && (!tc_fwd_t_tile(t) || bn != 64)) continue;
-                    for (int raster : {0, 1}) {
-                        TcConfig c = base;
-                        c.block_n = bn;
-                        c.stages = 0;  // maximum for this width
-                        c.raster = raster;
-                        c.algo = algo;
-                        cands.push_back(c);
-                    }
+                    // the im2col ring depth is a launch parameter (0: the most that
+                    // fits); the band kernels size their rings from the layer
+                    const std::vector<int> stage_set = algo == GBCONV_ALGO_IM2COL
+                                                           ? std::vector<int>{0, 4, 3}
+                                                           : std::vector<int>{0};
+                    for (int stages : stage_set)
+                        for (int raster : {0, 1}) {
+                            TcConfig c = base;
+                            c.block_n = bn;
+                            c.stages = stages;
+                            c.raster = raster;
+                            c.algo = algo;
+                            cands.push_back(c);
+                        }
                 }
+            }
+            // the pixel-major band kernel picks its own tile: one SM, or a pair
+            for (int form : {1, 2})
+                if (tc_fwd_p_form(t, form) == form) {
+                    TcConfig c = base;
+                    c.algo = form == 1 ? GBCONV_ALGO_PBAND : GBCONV_ALGO_PBAND_PAIR;
+                    cands.push_back(c);
+                }
+        } else if (phases) {
+            // sub-pixel phases on the tensor cores, or the CUDA-core gather kernel
+            for (int algo : {GBCONV_ALGO_AUTO, GBCONV_ALGO_SIMT}) {
+                TcConfig c = base;
+                c.algo = algo;
+                cands.push_back(c);
             }
         } else {
             cands.push_back(base);
@@ -682,6 +797,10 @@ gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void
         std::lock_guard<std::mutex> lock(g_mu);
         g_tune[k] = best_c;
     }
+    {
+        const char *path = getenv("GBCONV_TUNE_CACHE");
+        if (path && *path) gbconv_tune_cache_save(path);
+    }
     if (best) {
         best->block_n = best_c.block_n;
         best->stages = best_c.stages;
@@ -712,8 +831,15 @@ gbconv_status_t gbconv_tune_cache_save(const char *path) {
     return GBCONV_OK;
 }
 
-// Reads the format written above: one entry object per line.
 gbconv_status_t gbconv_tune_cache_load(const char *path) {
+    load_env_cache_once();  // an explicit load takes precedence over the environment's
+    return gbc::load_cache_file(path);
+}
+
+}  // extern "C"
+
+// Reads the format gbconv_tune_cache_save writes: one entry object per line.
+gbconv_status_t gbc::load_cache_file(const char *path) {
     if (!path) return GBCONV_ERR_INVALID_ARG;
     FILE *f = fopen(path, "r");
     if (!f) return GBCONV_ERR_INVALID_ARG;
@@ -740,6 +866,8 @@ gbconv_status_t gbconv_tune_cache_load(const char *path) {
     for (auto &kv : add) g_tune[kv.first] = kv.second;
     return GBCONV_OK;
 }
+
+extern "C" {
 
 gbconv_status_t gbconv_get_device_error(gbconv_stream_t stream) {
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
@@ -775,7 +903,7 @@ gbconv_status_t gbconv_debug_set(int32_t key, int64_t value) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (key == GBCONV_DEBUG_WAIT_LIMIT_NS) {
         if (value < 0) return GBCONV_ERR_INVALID_ARG;
-        g_wait_ns = value == 0 ? 2000000000ull : (uint64_t)value;
+        g_wait_ns = value == 0 ? default_wait_ns() : (uint64_t)value;
         return GBCONV_OK;
     }
     if (key == GBCONV_DEBUG_SKIP_LOADS) {
@@ -815,18 +943,32 @@ gbconv_status_t conv2d_dgrad_noalloc(const gbconv_problem_t *prob, const void *d
     if (d.in_dtype == GBCONV_E4M3 || d.out_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
     if (d.in_dtype == GBCONV_F32 && d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const TcConfig cfg = config_for(GBCONV_OP_DGRAD, *prob, d);
     Dims t;
-    if (!dgrad_as_fwd(d, &t)) return launch_simt_dgrad(d, dy, w, dx, st);  // no scratch used
+    const bool rotated = cfg.algo != GBCONV_ALGO_SIMT && dgrad_as_fwd(d, &t);
+    const bool phases = cfg.algo != GBCONV_ALGO_SIMT && !rotated && tc_dgrad_t_supported(d);
+    if (!rotated && !phases) return launch_simt_dgrad(d, dy, w, dx, st);  // no scratch used
+    // the tensor-core forms keep the filter, rotated (stride 1) or transposed
+    // (sub-pixel phases of strided layers), in the static scratch
     const size_t need = (size_t)d.K * d.R * d.S * d.C * 2;
     if (need > (size_t)GBCONV_DGRAD_STATIC_SCRATCH_BYTES) return GBCONV_ERR_WORKSPACE;
     if (!aligned16(dy) || !aligned16(dx)) return GBCONV_ERR_ALIGNMENT;
     void *scratch = nullptr;
     s = dgrad_static_scratch(&scratch);
     if (s != GBCONV_OK) return s;
+    if (phases) {
+        s = launch_transpose_filter(d, w, scratch, st);
+        if (s != GBCONV_OK) return s;
+        return launch_tc_dgrad_t(d, dy, scratch, dx, st);
+    }
     s = launch_rotate_filter(d, w, scratch, st);
     if (s != GBCONV_OK) return s;
-    return launch_tc_fwd(t, config_for(GBCONV_OP_DGRAD, *prob, d), dy, scratch, nullptr, nullptr,
-                         nullptr, dx, st);
+    return launch_tc_fwd(t, cfg, dy, scratch, nullptr, nullptr, nullptr, dx, st);
+}
+
+gbconv_status_t gbconv_measure_ffma_tflops(int64_t iters, double *tflops, gbconv_stream_t stream) {
+    if (iters < 1 || !tflops) return GBCONV_ERR_INVALID_ARG;
+    return measure_ffma_rate(iters, tflops, static_cast<cudaStream_t>(stream));
 }
 
 int32_t gbconv_version(void) { return 10000; }

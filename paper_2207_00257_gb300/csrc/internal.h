@@ -88,6 +88,11 @@ gbconv_status_t launch_bn_fold(int K, const float *gamma, const float *bn_beta, 
                                float *shift, cudaStream_t st);
 // zeroes dx at rows u*h' + a, columns v*w' + b (NHWC, out_dtype of d)
 gbconv_status_t launch_zero_phase(const Dims &d, void *dx, int a, int b, cudaStream_t st);
+// out[i] = y[i] > 0 ? g[i] : 0 (F32/BF16 each; out may alias g when the types match)
+gbconv_status_t launch_relu_grad(const void *y, int y_dtype, const void *g, int g_dtype, void *out,
+                                 int out_dtype, long long n, cudaStream_t st);
+// FFMA throughput of the current device (synchronous; CUDA events on st)
+gbconv_status_t measure_ffma_rate(long long iters, double *tflops, cudaStream_t st);
 gbconv_status_t launch_quantize_e4m3(const void *in, int in_dtype, long long rows, long long len,
                                      uint8_t *out, float *scale, cudaStream_t st);
 
@@ -121,6 +126,13 @@ int tc_fwd_t_tile(const Dims &d);  // output-channel tile (64 / 128), 0 if unsui
 gbconv_status_t launch_tc_fwd_t(const Dims &d, const void *x, const void *w, const float *bias,
                                 const float *x_scale, const float *w_scale, void *y,
                                 cudaStream_t st, const Fused &fz = Fused{});
+// tc_fwd_p.cu: pixel-major band kernel (BF16, multi-tap, K <= 128, strides up
+// to 4 by phases, resident filter) on one SM (form 1) or a pair of SMs (form 2).
+// tc_fwd_p_form: the form it would take (want 1 or 2: only that form; 0: the
+// automatic choice), 0 when it cannot take the layer.
+int tc_fwd_p_form(const Dims &d, int want);
+gbconv_status_t launch_tc_fwd_p(const Dims &d, int form, const void *x, const void *w,
+                                const float *bias, void *y, cudaStream_t st);
 gbconv_status_t launch_tc_grouped(int count, const Dims *d, const TcConfig *cfg,
                                   const void *const *x, const void *const *w,
                                   const float *const *bias, void *const *y, cudaStream_t st);

@@ -615,6 +615,18 @@ gbconv_status_t launch_tc_fwd(const Dims &d, const TcConfig &cfg_in, const void 
     // pixel-major tiles would be ragged (K not a multiple of 256) and the filter
     // cannot stay resident in the pixel-major band kernel (measured: K = 192 is
     // 30 % faster on the band kernel, K = 256 20-35 % slower).
+    // The pixel-major band kernel (output pixels on M, filter resident, one SM
+    // or a pair of SMs per MMA) runs when the config asks for it (multi-tap
+    // BF16 layers with up to 128 output channels, no fused scale or residual).
+    // The automatic choice does not take it: on the ResNet 3x3 layers it
+    // measured slower than the transposed band kernel (L2 17.4 against 15.0
+    // us, the strided L4 20.2 against 14.0 us).
+    if (cfg.algo == GBCONV_ALGO_PBAND || cfg.algo == GBCONV_ALGO_PBAND_PAIR) {
+        const int want = cfg.algo == GBCONV_ALGO_PBAND ? 1 : 2;
+        const int form = (fz.alpha || fz.z) ? 0 : tc_fwd_p_form(d, want);
+        if (form) return launch_tc_fwd_p(d, form, x, w, bias, y, st);
+        return GBCONV_ERR_UNSUPPORTED;
+    }
     if (cfg.algo == GBCONV_ALGO_SHIFT_T ||
         (cfg.algo == GBCONV_ALGO_AUTO && d.R * d.S > 1 &&
          (d.K <= 128 || (d.K % 256 != 0 && !tc_fwd_shift_preferred(d, cfg.block_n))))) {

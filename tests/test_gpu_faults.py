@@ -19,8 +19,11 @@ def _lib():
     __graft_entry__.build()
 
 
-def test_wait_timeout_reported_and_context_survives():
-    sh = ConvShape(2, 64, 9, 9, 64, 3, 3, 1, 1, 1)
+@pytest.mark.parametrize("sh", [ConvShape(2, 64, 9, 9, 64, 3, 3, 1, 1, 1),      # one SM per tile
+                                ConvShape(3, 128, 9, 9, 128, 3, 3, 1, 1, 1),    # SM pairs
+                                ConvShape(2, 64, 9, 9, 256, 3, 3, 1, 1, 1)],    # 256 channels
+                         ids=["pband", "pband-pair", "k256"])
+def test_wait_timeout_reported_and_context_survives(sh):
     x, w, b, _ = make_inputs(sh, 40)
     xb, wb, bb = x.bfloat16().cuda(), w.bfloat16().cuda(), b.cuda()
     ref = F.conv2d(xb, wb, bb, 1, 1, 1, True)
@@ -29,6 +32,7 @@ def test_wait_timeout_reported_and_context_survives():
     B.check(B.gbconv_debug_set(B.GBCONV_DEBUG_SKIP_LOADS, 1), "debug")
     try:
         F.conv2d(xb, wb, bb, 1, 1, 1, True)
+        # every CTA gives up on its first wait: the call ends within the limits
         st = B.gbconv_get_device_error(torch.cuda.current_stream().cuda_stream)
         assert st == B.GBCONV_ERR_TIMEOUT
     finally:
