@@ -28,6 +28,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# max |y - y_oracle| / sum|x||w| allowed for BF16 outputs (twice the 2^-9 output rounding)
+PARITY_TOL_BF16_OUT = 4e-3
+
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -293,6 +296,9 @@ def main():
     ap.add_argument("--sections", default="fp32,fp8,grouped,backward,fused,groups,nll",
                     help="comma list of extra workloads to run after the headline layer set")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--jsonl", default=os.environ.get("GBCONV_BENCH_JSONL"),
+                    help="also append one JSON record per result (headline, each layer, each "
+                         "extra workload) to this file (default: $GBCONV_BENCH_JSONL, else none)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -393,13 +399,43 @@ def run_ours(args, rank, world, local):
                 out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
     sampler.stop()
     out["clocks"] = sampler.summary(*clocks_window)
+    parity_bad = {}
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(layers, torch)
+        # the step's outputs against the oracle: BF16 output rounding bounds the
+        # normalised error by 2^-9; anything above twice that is a wrong result
+        parity_bad = {k: v for k, v in out["cpu_baseline"]["max_normalised_err_bf16_vs_oracle"].items()
+                      if not v <= PARITY_TOL_BF16_OUT}
+        out["parity_ok"] = not parity_bad
     if rank == 0:
         print(json.dumps(out), flush=True)
+        if args.jsonl:
+            write_records(args.jsonl, out)
+    if parity_bad:
+        sys.stderr.write(f"bench: outputs differ from the FP64 oracle beyond {PARITY_TOL_BF16_OUT}: "
+                         f"{parity_bad}\n")
+        raise SystemExit(3)
     if dist_on:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def write_records(path, out):
+    """One JSON line per result: the headline, each layer of the step, each
+    extra workload; every record carries the run's workload, clocks and
+    oracle baseline so that it stands on its own."""
+    common = {"time": time.strftime("%Y-%m-%dT%H:%M:%S"), "n_gpus": out["n_gpus"],
+              "clocks": out.get("clocks"), "cpu_baseline": out.get("cpu_baseline")}
+    recs = [dict(common, kind="headline", **{k: out[k] for k in (
+        "metric", "value", "unit", "ms_per_step", "dtype", "config", "roofline", "e2e")})]
+    for row in out.get("layers", []):
+        recs.append(dict(common, kind="layer", **row))
+    for name in ("fp32", "fp8", "grouped", "backward", "fused", "groups", "nll"):
+        if name in out:
+            recs.append(dict(common, kind=name, result=out[name]))
+    with open(path, "a") as f:
+        for r in recs:
+            f.write(json.dumps(r) + "\n")
 
 
 def e2e_resnet(layers, torch, dist_on, world, steps):
@@ -446,8 +482,13 @@ def bench_fp32(torch, dev, args, dist_on, pk):
     res = bench_layers(layers, steps, 3, 2, torch, dist_on)
     flops = sum(l.sh.flops for l in layers)
     prop = torch.cuda.get_device_properties(dev)
-    # FP32 CUDA-core peak: 128 FFMA lanes per SM x 2 flops x SMs x max SM clock
-    fp32_peak = 2 * 128 * prop.multi_processor_count * 2.070e9 / 1e12
+    # FP32 CUDA-core peak: 128 FFMA lanes per SM x 2 flops x SMs x max SM clock,
+    # and the FFMA probe's measured rate beside it (the roofline uses the probe)
+    fp32_nominal = 2 * 128 * prop.multi_processor_count * 2.070e9 / 1e12
+    from paper_2207_00257_gb300 import binding as B
+    st, fp32_measured = B.gbconv_measure_ffma_tflops(20000, torch.cuda.current_stream().cuda_stream)
+    B.check(st, "gbconv_measure_ffma_tflops")
+    fp32_peak = fp32_measured
     v = flops / (res["ms_per_step"] * 1e-3) / 1e12
     rows = []
     for lay, us in zip(layers, res["launch_us"]):
@@ -457,8 +498,11 @@ def bench_fp32(torch, dev, args, dist_on, pk):
     torch.cuda.empty_cache()
     return {"tflops": round(v, 2), "ms_per_step": round(res["ms_per_step"], 4),
             "fp32_peak_tflops": round(fp32_peak, 1),
-            "fp32_peak_note": "2 x 128 FFMA lanes x SMs x 2070 MHz (max clock)",
-            "frac_of_fp32_peak": round(v / fp32_peak, 4), "layers": rows,
+            "fp32_peak_note": "measured: FFMA probe kernel (gbconv_measure_ffma_tflops, CUDA events)",
+            "fp32_nominal_tflops": round(fp32_nominal, 1),
+            "fp32_nominal_note": "2 x 128 FFMA lanes x SMs x 2070 MHz (max clock)",
+            "frac_of_fp32_peak": round(v / fp32_peak, 4),
+            "frac_of_fp32_nominal": round(v / fp32_nominal, 4), "layers": rows,
             "kernel": "simt_igemm (FP32 FFMA, no tensor cores)"}
 
 
@@ -504,15 +548,50 @@ def bench_fp8(torch, dev, args, dist_on, pk):
     conv_b2b_us = res_c["ms_per_step"] * 1e3
     tf_conv = sh.flops / (conv_b2b_us * 1e-6) / 1e12
     tf_step = sh.flops / (res["ms_per_step"] * 1e-3) / 1e12
-    fp8_peak = 2 * pk["bf16_tflops"]
+    fp8_peak, fp8_note = measure_fp8_peak(torch, dev)
     return {"workload": sh.tag, "tflops_conv_kernel": round(tf_conv, 1),
             "tflops_with_activation_quantisation": round(tf_step, 1),
             "conv_us": round(conv_b2b_us, 2),
             "conv_us_event_separated": round(conv_us, 2),
             "quant_us": round(res["launch_us"][0], 2),
             "fp8_peak_tflops": round(fp8_peak, 1),
-            "fp8_peak_note": "2 x measured BF16 burst (the dense FP8:BF16 tensor-rate ratio)",
+            "fp8_peak_note": fp8_note,
             "frac_of_fp8_peak": round(tf_conv / fp8_peak, 4)}
+
+
+def measure_fp8_peak(torch, dev):
+    """Dense E4M3 tensor-core peak of this GPU: cuBLASLt through
+    torch._scaled_mm on 8192^3 (per-tensor scales, BF16 output), best of 10
+    launches timed with CUDA events after 3 warm-ups; the larger of the two
+    accumulation modes."""
+    n = 8192
+    g = torch.Generator(device=dev).manual_seed(11)
+    a = torch.randn(n, n, device=dev, generator=g).to(torch.float8_e4m3fn)
+    b = torch.randn(n, n, device=dev, generator=g).to(torch.float8_e4m3fn).t()  # column-major
+    one = torch.ones((), device=dev, dtype=torch.float32)
+    best = {}
+    for fast in (False, True):
+        def mm():
+            return torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16,
+                                    use_fast_accum=fast)
+        for _ in range(3):
+            mm()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(10):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mm()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        best[fast] = 2 * n ** 3 / (min(ms) * 1e-3) / 1e12
+    del a, b
+    torch.cuda.empty_cache()
+    peak = max(best.values())
+    return peak, (f"measured: torch._scaled_mm E4M3 {n}^3 (cuBLASLt), best of 10, CUDA events; "
+                  f"{best[False]:.0f} TF (fp32 accumulate) / {best[True]:.0f} TF (fast accumulate)")
 
 
 def bench_grouped(torch, dev, args, dist_on, pk):
@@ -589,8 +668,8 @@ def bench_backward(torch, dev, args, dist_on, pk):
             s.launch = f
 
     # data gradient of the strided ResNet layer (3x3 stride 2, 128 -> 128, 56 -> 28):
-    # sub-pixel phases on the tensor cores, and the CUDA-core gather kernel
-    # (which the allocation-free entry point uses for strided layers)
+    # sub-pixel phases on the tensor cores (workspace, and the allocation-free
+    # entry point's static scratch), and the CUDA-core gather kernel
     from paper_2207_00257_gb300.synth import resnet_layers
     s2 = resnet_layers(32)[3]
     _, w2, _, g2 = make_inputs(s2, 6, grad=True)
@@ -605,13 +684,22 @@ def bench_backward(torch, dev, args, dist_on, pk):
         B.check(B.conv2d_dgrad(prob2, g2b.data_ptr(), w2b.data_ptr(), dx2.data_ptr(),
                                wsd2.data_ptr(), nd2, stream), "dgrad s2")
 
-    def dgrad_s2_cuda_cores(i, stream):
+    def dgrad_s2_noalloc(i, stream):
         B.check(B.conv2d_dgrad_noalloc(prob2, g2b.data_ptr(), w2b.data_ptr(), dx2.data_ptr(),
-                                       stream), "dgrad s2 (CUDA cores)")
+                                       stream), "dgrad s2 (static scratch)")
 
     steps = max(3, min(args.steps, 20))
-    res = bench_layers([L(dgrad), L(wgrad), L(dgrad_s2), L(dgrad_s2_cuda_cores)], steps, 3, 1,
+    res = bench_layers([L(dgrad), L(wgrad), L(dgrad_s2), L(dgrad_s2_noalloc)], steps, 3, 1,
                        torch, dist_on)
+    # the CUDA-core gather kernel on the same strided layer, by its stored config
+    B.check(B.gbconv_set_config(B.GBCONV_OP_DGRAD, prob2,
+                                B.gbconv_config_t(0, 0, 0, 0, B.GBCONV_ALGO_SIMT)), "set_config")
+    try:
+        res_cc = bench_layers([L(dgrad_s2)], max(3, min(args.steps, 5)), 3, 1, torch, dist_on)
+    finally:
+        B.check(B.gbconv_set_config(B.GBCONV_OP_DGRAD, prob2,
+                                    B.gbconv_config_t(0, 0, 0, 0, B.GBCONV_ALGO_AUTO)), "set_config")
+    cc_us = res_cc["launch_us"][0]
     f = sh.flops
     f2 = s2.flops
     return {"workload": sh.tag, "dgrad_us": round(res["launch_us"][0], 1),
@@ -622,8 +710,9 @@ def bench_backward(torch, dev, args, dist_on, pk):
             "dgrad_stride2": {"workload": "dgrad_" + s2.tag,
                               "subpixel_tc_us": round(res["launch_us"][2], 1),
                               "subpixel_tc_tflops": round(f2 / (res["launch_us"][2] * 1e-6) / 1e12, 1),
-                              "cuda_core_us": round(res["launch_us"][3], 1),
-                              "cuda_core_tflops": round(f2 / (res["launch_us"][3] * 1e-6) / 1e12, 2)}}
+                              "subpixel_tc_static_scratch_us": round(res["launch_us"][3], 1),
+                              "cuda_core_us": round(cc_us, 1),
+                              "cuda_core_tflops": round(f2 / (cc_us * 1e-6) / 1e12, 2)}}
 
 
 def bench_fused(torch, dev, args, dist_on, pk):
