@@ -170,58 +170,6 @@ __device__ __forceinline__ Tile tdecode(const TParams &p, int tile) {
     return t;
 }
 
-// The MMAs of one band with a resident filter: NT taps x 4 K-steps, in
-// straight-line code. The filter tiles of consecutive taps are consecutive
-// (stored in MMA order), the band shifts come from a shared-memory table. The
-// single issuing thread must keep up with the tensor core, whose queue of MMA
-// instructions is short, so nothing but MMAs and additions runs between them.
-template <int NT, int KT, bool FP8>
-__device__ __forceinline__ void t_issue_taps(uint32_t d, uint64_t a0, uint64_t b0, const uint16_t *bsh,
-                                             uint32_t idesc, uint32_t &accum) {
-    constexpr uint32_t ASTEP = KT * 128 / 16;  // one filter tile in descriptor units
-    uint32_t bo[NT];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) bo[t] = (uint32_t)bsh[t] << 3;  // 128-byte rows = 8 units
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint64_t ad = a0 + t * ASTEP + 2 * k, bd = b0 + bo[t] + 2 * k;
-            if (FP8)
-                ptx::mma_f8(d, ad, bd, idesc, accum);
-            else
-                ptx::mma_f16(d, ad, bd, idesc, accum);
-            accum = 1;
-        }
-}
-
-template <int KT, bool FP8>
-__device__ __forceinline__ void t_issue_band(int nt, uint32_t d, uint64_t a0, uint64_t b0,
-                                             const uint16_t *bsh, uint32_t idesc, uint32_t &accum) {
-    constexpr uint32_t ASTEP = KT * 128 / 16;
-    switch (nt) {
-        case 1: t_issue_taps<1, KT, FP8>(d, a0, b0, bsh, idesc, accum); return;
-        case 2: t_issue_taps<2, KT, FP8>(d, a0, b0, bsh, idesc, accum); return;
-        case 3: t_issue_taps<3, KT, FP8>(d, a0, b0, bsh, idesc, accum); return;
-        case 4: t_issue_taps<4, KT, FP8>(d, a0, b0, bsh, idesc, accum); return;
-        case 6: t_issue_taps<6, KT, FP8>(d, a0, b0, bsh, idesc, accum); return;
-        case 9: t_issue_taps<9, KT, FP8>(d, a0, b0, bsh, idesc, accum); return;
-        default:
-            for (int t0 = 0; t0 < nt; t0 += 4) {  // other tap counts in runs of up to four
-                const int n = nt - t0 < 4 ? nt - t0 : 4;
-                const uint64_t a = a0 + (uint64_t)t0 * ASTEP;
-                if (n == 4)
-                    t_issue_taps<4, KT, FP8>(d, a, b0, bsh + t0, idesc, accum);
-                else if (n == 3)
-                    t_issue_taps<3, KT, FP8>(d, a, b0, bsh + t0, idesc, accum);
-                else if (n == 2)
-                    t_issue_taps<2, KT, FP8>(d, a, b0, bsh + t0, idesc, accum);
-                else
-                    t_issue_taps<1, KT, FP8>(d, a, b0, bsh + t0, idesc, accum);
-            }
-    }
-}
-
 // FUSED: the epilogue also applies the per-channel scale and the residual.
 // OPH: data-gradient launch, tiles grouped by output phase (n_ophase > 0).
 template <int KT, bool FP8, bool FUSED, bool OPH>
@@ -264,8 +212,6 @@ __global__ void __launch_bounds__(nthreads<KT>(), 1) tc_fwd_t_kernel(const __gri
     const int w_tiles = prm.RS * prm.c_blocks;
     const int wper = (w_tiles + MAX_WRES - 1) / MAX_WRES;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    // band shift of every tap-table entry (bytes 576..831 of the barrier block)
-    uint16_t *s_shift = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(bars) + 576);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t lim = prm.guard.wait_ns;
@@ -289,7 +235,6 @@ __global__ void __launch_bounds__(nthreads<KT>(), 1) tc_fwd_t_kernel(const __gri
         }
         ptx::mbar_init(done, 1);
         *abort_flag = 0;
-        for (int i = 0; i < prm.RS; ++i) s_shift[i] = prm.tap_shift[i];  // RS = tap-table length
         ptx::fence_mbar_init();
     }
     if (warp == 1) {
@@ -504,25 +449,34 @@ __global__ void __launch_bounds__(nthreads<KT>(), 1) tc_fwd_t_kernel(const __gri
                             ptx::sdesc_kmajor_sw128(ptx::smem_addr(sA + sa * prm.band_stride));
                         const int t0 = f ? prm.ph_end[f - 1] : 0, t1 = prm.ph_end[f];
                         if (prm.w_resident) {
-                            if (local == 0 || OPH) {
-                                // the forward's first tile uses every group; a data-gradient
-                                // tile uses its phase's groups, first seen on any tile: wait
-                                // for the groups of this band's taps before its MMAs
-                                const int g0 = (cb * prm.RS + t0) / wper, g1 = (cb * prm.RS + t1 - 1) / wper;
-                                for (int grp = g0; ok && grp <= g1; ++grp)
+                            const bool first_use = local == 0 || OPH;
+                            uint64_t ad = adb + (uint64_t)((cb * prm.RS + t0) * (W_TILE >> 4));
+                            for (int ti = t0; ti < t1; ++ti) {
+                                if (first_use) {
+                                    // the forward's first tile uses every group; a data-gradient
+                                    // tile uses its phase's groups, first seen on any tile
+                                    const int grp = (cb * prm.RS + ti) / wper;
                                     if (!((wres_seen >> grp) & 1u)) {
                                         if (!ptx::mbar_wait(&wres[grp], 0, lim, abort_flag)) {
                                             fail();
                                             ok = false;
                                             break;
                                         }
+                                        ptx::tc_fence_after();
                                         wres_seen |= 1u << grp;
                                     }
-                                if (!ok) break;
-                                ptx::tc_fence_after();
+                                }
+                                const uint64_t bd = bdb + ((uint64_t)prm.tap_shift[ti] << 3);
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    if (FP8)
+                                        ptx::mma_f8(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                                    else
+                                        ptx::mma_f16(d, ad + 2 * k, bd + 2 * k, idesc, accum);
+                                    accum = 1;
+                                }
+                                ad += W_TILE >> 4;
                             }
-                            t_issue_band<KT, FP8>(t1 - t0, d, adb + (uint64_t)((cb * prm.RS + t0) * (W_TILE >> 4)),
-                                                  bdb, s_shift + t0, idesc, accum);
                         } else {
                             for (int ti = t0; ti < t1; ++ti) {
                                 if (gi == 0) {  // first tile of a stage
