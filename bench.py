@@ -439,40 +439,89 @@ def write_records(path, out):
 
 
 def e2e_resnet(layers, torch, dist_on, world, steps):
-    """Same metric through the user call: per step, pinned host -> device copy
-    of each layer's input, conv2d_fwd, device -> pinned host copy of y."""
+    """Same metric through the user call, with the copies in the timed region:
+    per step and layer, the pinned host -> device copy of its input,
+    conv2d_fwd through the public functional API, and the device -> pinned
+    host copy of y. The copies run on their own streams (one per direction,
+    so both copy engines and the C2C link's two directions work at once) and
+    the inputs and outputs are double-buffered across steps: the upload of the
+    next layer overlaps the convolution of this one and the download of the
+    previous one. The serial form (everything on one stream) is timed too."""
     from paper_2207_00257_gb300 import functional as F
     hx = [l.xs[0].cpu().pin_memory() for l in layers]
     hy = [torch.empty(l.ys[0].shape, dtype=l.ys[0].dtype).pin_memory() for l in layers]
-    dx = [torch.empty_like(l.xs[0]) for l in layers]
-    stream = torch.cuda.current_stream()
+    dx = [[torch.empty_like(l.xs[0]) for _ in range(2)] for l in layers]
+    dy = [[torch.empty_like(l.ys[0]) for _ in range(2)] for l in layers]
+    s_in, s_c, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()
+    h2d_done = [[ev(), ev()] for _ in layers]
+    conv_done = [[ev(), ev()] for _ in layers]
+    d2h_done = [[ev(), ev()] for _ in layers]
+    first = [[True, True] for _ in layers]
 
-    def step():
+    def step(k):
+        b = k & 1
+        for i, l in enumerate(layers):
+            with torch.cuda.stream(s_in):
+                if not first[i][b]:
+                    s_in.wait_event(conv_done[i][b])  # the convolution of step k-2 has read it
+                dx[i][b].copy_(hx[i], non_blocking=True)
+                h2d_done[i][b].record(s_in)
+            with torch.cuda.stream(s_c):
+                s_c.wait_event(h2d_done[i][b])
+                if not first[i][b]:
+                    s_c.wait_event(d2h_done[i][b])  # the download of step k-2 has read y
+                F.conv2d(dx[i][b], l.w, l.b, l.sh.stride, l.sh.pad, l.sh.dil, True, "NHWC",
+                         out=dy[i][b])
+                conv_done[i][b].record(s_c)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(conv_done[i][b])
+                hy[i].copy_(dy[i][b], non_blocking=True)
+                d2h_done[i][b].record(s_out)
+            first[i][b] = False
+
+    def serial_step():
+        st = torch.cuda.current_stream()
         for l, h, d, o in zip(layers, hx, dx, hy):
-            d.copy_(h, non_blocking=True)
-            y = F.conv2d(d, l.w, l.b, l.sh.stride, l.sh.pad, l.sh.dil, True, "NHWC", out=l.ys[0])
+            d[0].copy_(h, non_blocking=True)
+            y = F.conv2d(d[0], l.w, l.b, l.sh.stride, l.sh.pad, l.sh.dil, True, "NHWC", out=l.ys[0])
             o.copy_(y, non_blocking=True)
 
-    for _ in range(2):
-        step()
+    def timed(run, n):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist_on:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.current_stream()
+        e0.record(t0)
+        for sx in (s_in, s_c, s_out):
+            sx.wait_event(e0)
+        for k in range(n):
+            run(k)
+        for sx in (s_in, s_c, s_out):
+            t0.wait_stream(sx)
+        e1.record(t0)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), torch, dist_on)
+
+    for k in range(4):  # warm-up, both forms
+        step(k)
+    serial_step()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist_on:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = max_over_ranks(e0.elapsed_time(e1), torch, dist_on)
+    ms = timed(lambda k: step(k + 4), steps)
+    ms_serial = timed(lambda k: serial_step(), steps)
     flops = sum(l.sh.flops for l in layers) * steps * world
     h2d = sum(t.numel() * t.element_size() for t in hx)
     d2h = sum(t.numel() * t.element_size() for t in hy)
     return {"value": round(flops / (ms * 1e-3) / 1e12, 2), "unit": "TFLOP/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
-            "ms_per_step": round(ms / steps, 4)}
+            "ms_per_step": round(ms / steps, 4),
+            "link_gbs": round((h2d + d2h) / (ms / steps * 1e-3) / 1e9, 1),
+            "pipeline": "H2D, compute and D2H on three streams, inputs/outputs double-buffered",
+            "serial_ms_per_step": round(ms_serial / steps, 4),
+            "serial_tflops": round(flops / (ms_serial * 1e-3) / 1e12, 2)}
 
 
 def bench_fp32(torch, dev, args, dist_on, pk):

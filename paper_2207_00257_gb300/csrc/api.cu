@@ -354,6 +354,8 @@ gbconv_status_t do_fwd(const Dims &d, const TcConfig &cfg, const void *x, const 
     if (d.G > 1) return do_fwd_groups(d, x, w, bias, x_scale, w_scale, y, st, fz);
     if (d.in_dtype == GBCONV_F32) {
         if (d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
+        if (cfg.algo != GBCONV_ALGO_SIMT && simt_fast_supported(d, x, w, y, fz.z))
+            return launch_simt_fast_fwd(d, x, w, bias, y, st, fz);
         return launch_simt_fwd(d, x, w, bias, y, st, fz);
     }
     if (cfg.algo == GBCONV_ALGO_SIMT) {  // the CUDA-core kernel on request (BF16 in)

@@ -53,6 +53,12 @@ gbconv_status_t cuda_status(cudaError_t e);
 // Forward with d.G >= 1 channel groups (one grid layer per group).
 gbconv_status_t launch_simt_fwd(const Dims &d, const void *x, const void *w, const float *bias,
                                 void *y, cudaStream_t st, const Fused &fz = Fused{});
+// simt_fast.cu: FP32 NHWC forward with C and K multiples of 4 (16-byte vectors,
+// 128 x 128 / 128 x 64 register-blocked tiles); simt_fast_supported checks
+// layout, dtypes, channel counts and pointer alignment (z: residual or null).
+bool simt_fast_supported(const Dims &d, const void *x, const void *w, const void *y, const void *z);
+gbconv_status_t launch_simt_fast_fwd(const Dims &d, const void *x, const void *w, const float *bias,
+                                     void *y, cudaStream_t st, const Fused &fz = Fused{});
 // nll.cu: negative log-likelihood loss (fp32 log-probabilities [N][C]).
 size_t nll_workspace_bytes(long long N);
 gbconv_status_t launch_nll_fwd(const float *logp, const int64_t *target, const float *weight,

@@ -335,3 +335,47 @@ def test_fp8_forward_algorithms(algo):
     finally:
         B.gbconv_shutdown()
     assert r["err_i"] <= TOL_BF16_OUT and r["err_ii"] <= TOL_FP8, r
+
+
+# ---------------- the FP32 NHWC fast path (C, K multiples of 4) ----------------
+
+FAST_F32_SHAPES = [
+    ConvShape(2, 64, 9, 11, 64, 3, 3, 1, 1, 1),        # ragged pixel tile, 64-column tile
+    ConvShape(1, 4, 7, 7, 4, 3, 3, 1, 1, 1),           # one channel vector, one output vector
+    ConvShape(2, 20, 10, 10, 68, 3, 3, 1, 1, 1),       # partial channel block, K past 64
+    ConvShape(2, 128, 12, 12, 128, 3, 3, 2, 1, 1),     # stride 2, 128-column tile
+    ConvShape(1, 64, 15, 13, 200, 3, 3, 1, 2, 2),      # dilation 2, two 128-column tiles
+    ConvShape(3, 256, 7, 7, 64, 1, 1, 1, 0, 1),        # 1x1
+    ConvShape(1, 32, 9, 16, 48, 5, 3, (2, 1), (2, 1), 1),  # rectangular filter, row stride
+]
+
+
+@pytest.mark.parametrize("sh", FAST_F32_SHAPES, ids=_id)
+def test_fp32_fast_path_matches_oracle(sh):
+    r = fwd_case(sh, torch.float32, relu=True, seed=160)
+    assert r["err_i"] <= TOL_F32, r["err_i"]
+
+
+def test_fp32_fast_path_integer_exact():
+    """Integer operands: every partial sum is exact in FP32, so the register-
+    blocked FFMA kernel equals the oracle bit for bit."""
+    sh = ConvShape(2, 64, 11, 10, 96, 3, 3, 1, 1, 1)
+    x, w, b, _ = make_inputs(sh, 161, x_dist=("int", -4, 4), w_dist=("int", -4, 4))
+    y = F.conv2d(x.cuda(), w.cuda(), b.cuda(), 1, 1, 1, False, "NHWC")
+    F.device_error()
+    ref = oracle.conv2d_fwd(oconv(sh), f64(x), f64(w), f64(b))
+    assert np.array_equal(f64(y), ref)
+
+
+def test_fp32_fast_path_fused_residual_in_place():
+    sh = ConvShape(2, 32, 8, 9, 64, 3, 3, 1, 1, 1)
+    x, w, b, _ = make_inputs(sh, 162)
+    g = torch.Generator().manual_seed(163)
+    alpha = torch.rand(sh.K, generator=g) + 0.5
+    z = torch.randn(sh.y_shape(), generator=g)
+    yz = z.clone().cuda()
+    F.conv2d_fused(x.cuda(), w.cuda(), b.cuda(), alpha.cuda(), yz, 1, 1, 1, True, out=yz)
+    F.device_error()
+    ref, bound = oracle.conv2d_fwd_fused(oconv(sh), f64(x), f64(w), f64(alpha), f64(b), f64(z),
+                                          relu=True, with_bound=True)
+    assert oracle.max_normalised_error(f64(yz), ref, bound) <= TOL_F32
