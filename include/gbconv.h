@@ -86,8 +86,10 @@ typedef enum { GBCONV_OP_FWD = 0, GBCONV_OP_DGRAD = 1, GBCONV_OP_WGRAD = 2 } gbc
  * and K/G multiples of 8 (16 for E4M3) runs each group on the tensor cores
  * in one persistent launch; depthwise NHWC (C/G = K/G = 1, C % 8 == 0) runs a
  * CUDA-core kernel with 16-byte channel vectors; the rest (F32/BF16 in) runs
- * the CUDA-core implicit GEMM per group. conv2d_dgrad, conv2d_wgrad and
- * conv2d_grouped return GBCONV_ERR_UNSUPPORTED for G > 1. */
+ * the CUDA-core implicit GEMM per group. conv2d_dgrad and conv2d_wgrad (and
+ * conv2d_dgrad_noalloc) take groups on the CUDA-core kernels (FP32
+ * accumulation, one grid layer per group); conv2d_grouped returns
+ * GBCONV_ERR_UNSUPPORTED for G > 1. */
 typedef struct {
     int32_t N, C, H, W, K, R, S;
     int32_t stride_h, stride_w;
@@ -143,8 +145,8 @@ gbconv_status_t gbconv_output_dims(const gbconv_problem_t *prob, int32_t *P, int
 /* Bytes of device workspace `op` needs for `prob` (0 when none). Host only.
  * FWD: 0. DGRAD: the filter rotated by 180 degrees with C and K exchanged
  * (tensor-core path, stride 1), rounded up to 256 bytes; 0 otherwise.
- * WGRAD: (split_k * K*R*S*C + 128 * K) fp32 partial sums (weight slices and
- * 128 bias slices), rounded up to 256 bytes. */
+ * WGRAD: (split_k * K*R*S*C/G + 128 * K) fp32 partial sums (weight slices
+ * and 128 bias slices), rounded up to 256 bytes. */
 gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, size_t *bytes);
 
 /* Forward convolution (paper Sec. 5.B, forward pass of a convolutional layer).

@@ -224,7 +224,7 @@ size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 int wgrad_default_slices(const Dims &d) {
     // about eight CTAs per SM of a 152-SM part, at most 64 slices, and no
     // more slices than the reduction has 16-pixel runs
-    long long tiles = (long long)((d.K + 127) / 128) * ((d.C + 63) / 64) * d.R * d.S;
+    long long tiles = (long long)d.G * ((d.K / d.G + 127) / 128) * ((d.C / d.G + 63) / 64) * d.R * d.S;
     long long runs = (long long)d.N * d.P * ((d.Q + 15) / 16);
     long long s = (1216 + tiles - 1) / tiles;
     s = std::min<long long>(s, 64);
@@ -236,13 +236,13 @@ TcConfig config_for(int op, const gbconv_problem_t &p, const Dims &d) {
     TcConfig c{};
     if (tuned(op, p, &c)) return c;
     if (op == GBCONV_OP_WGRAD) {
-        if (tc_wgrad_supported(d)) return tc_wgrad_default_config(d);
+        if (d.G == 1 && tc_wgrad_supported(d)) return tc_wgrad_default_config(d);
         c.split_k = wgrad_default_slices(d);
         return c;
     }
     if (op == GBCONV_OP_DGRAD) {
         Dims t;
-        if (dgrad_as_fwd(d, &t)) return tc_fwd_default_config(t);
+        if (d.G == 1 && dgrad_as_fwd(d, &t)) return tc_fwd_default_config(t);
         return c;
     }
     if (tc_fwd_supported(d)) return tc_fwd_default_config(d);
@@ -254,7 +254,7 @@ TcConfig config_for(int op, const gbconv_problem_t &p, const Dims &d) {
 constexpr int BIAS_SLICES = 128;
 
 size_t wgrad_ws_bytes(const Dims &d, int slices) {
-    size_t kcrs = (size_t)d.K * d.C * d.R * d.S;
+    size_t kcrs = (size_t)d.K * (d.C / d.G) * d.R * d.S;
     return round256(((size_t)slices * kcrs + (size_t)BIAS_SLICES * d.K) * sizeof(float));
 }
 
@@ -375,7 +375,8 @@ gbconv_status_t do_dgrad(const Dims &d, const TcConfig &cfg, const void *dy, con
     if ((long long)d.N * d.H * d.W == 0) return GBCONV_OK;
     if (d.in_dtype == GBCONV_E4M3 || d.out_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
     if (d.in_dtype == GBCONV_F32 && d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
-    if (cfg.algo == GBCONV_ALGO_SIMT) return launch_simt_dgrad(d, dy, w, dx, st);
+    // channel groups, and the CUDA-core kernel on request
+    if (d.G > 1 || cfg.algo == GBCONV_ALGO_SIMT) return launch_simt_dgrad(d, dy, w, dx, st);
     Dims t;
     if (dgrad_as_fwd(d, &t)) {
         size_t need = round256((size_t)d.K * d.R * d.S * d.C * 2);
@@ -401,8 +402,8 @@ gbconv_status_t do_dgrad(const Dims &d, const TcConfig &cfg, const void *dy, con
 gbconv_status_t do_wgrad(const Dims &d, const TcConfig &cfg, const void *x, const void *dy,
                          float *dw, float *db, void *ws, size_t ws_bytes, cudaStream_t st) {
     if (d.in_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
-    const long long kcrs = (long long)d.K * d.C * d.R * d.S;
-    const bool tc = tc_wgrad_supported(d) && aligned16(x) && aligned16(dy) && aligned16(ws);
+    const long long kcrs = (long long)d.K * (d.C / d.G) * d.R * d.S;  // the filter holds C/G channels
+    const bool tc = d.G == 1 && tc_wgrad_supported(d) && aligned16(x) && aligned16(dy) && aligned16(ws);
     int slices = std::max(1, cfg.split_k);
     if (slices > 1024) return GBCONV_ERR_INVALID_ARG;
     // the tensor-core kernel gives every slice at least one 64-pixel step
@@ -474,10 +475,9 @@ gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, 
         if (nchw_bf16(d)) *bytes = nchw_ws_bytes(d);
         return GBCONV_OK;
     }
-    if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;  // grouped gradients are not implemented
     if (op == GBCONV_OP_DGRAD) {
         Dims t;
-        if (dgrad_as_fwd(d, &t) || tc_dgrad_t_supported(d))
+        if (d.G == 1 && (dgrad_as_fwd(d, &t) || tc_dgrad_t_supported(d)))
             *bytes = round256((size_t)d.K * d.R * d.S * d.C * 2);
         return GBCONV_OK;
     }
@@ -579,7 +579,6 @@ gbconv_status_t conv2d_dgrad(const gbconv_problem_t *prob, const void *dy, const
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
-    if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;
     if (d.N == 0) return GBCONV_OK;  // empty batch: dx is empty
     if (!dy || !w || !dx || dx == dy || dx == w) return GBCONV_ERR_INVALID_ARG;
     const TcConfig c = config_for(GBCONV_OP_DGRAD, *prob, d);
@@ -594,7 +593,6 @@ gbconv_status_t conv2d_wgrad(const gbconv_problem_t *prob, const void *x, const 
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
-    if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;
     if (!dw || (d.N > 0 && (!x || !dy))) return GBCONV_ERR_INVALID_ARG;
     const TcConfig c = config_for(GBCONV_OP_WGRAD, *prob, d);
     s = do_wgrad(d, c, x, dy, dw, db, ws, ws_bytes, static_cast<cudaStream_t>(stream));
@@ -939,10 +937,10 @@ gbconv_status_t conv2d_dgrad_noalloc(const gbconv_problem_t *prob, const void *d
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
-    if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;
     if (d.N == 0) return GBCONV_OK;
     if (!dy || !w || !dx || dx == dy || dx == w) return GBCONV_ERR_INVALID_ARG;
     if (d.in_dtype == GBCONV_E4M3 || d.out_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
+    if (d.G > 1) return launch_simt_dgrad(d, dy, w, dx, static_cast<cudaStream_t>(stream));
     if (d.in_dtype == GBCONV_F32 && d.out_dtype != GBCONV_F32) return GBCONV_ERR_UNSUPPORTED;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const TcConfig cfg = config_for(GBCONV_OP_DGRAD, *prob, d);

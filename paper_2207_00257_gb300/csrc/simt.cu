@@ -258,8 +258,9 @@ struct DgradLoader {
     const Ti *g;
     const Ti *w;
     To *dx;
-    int kb;  // output-channel blocks of 16
+    int kb;  // output-channel blocks of 16 (of one group)
     int m0, n0, t;
+    int cx0, k0g;  // this group's first input and output channel (grid layer z = group)
     long long gb[8];
     int hh[8], wq[8];
 
@@ -267,6 +268,8 @@ struct DgradLoader {
         t = tid;
         m0 = blockIdx.x * BM;
         n0 = blockIdx.y * BN;
+        cx0 = blockIdx.z * d.Cg;
+        k0g = blockIdx.z * d.Kg;
         const long long M = (long long)d.N * d.H * d.W;
         const int cnt = NHWC ? 8 : 1;
         for (int i = 0; i < cnt; ++i) {
@@ -304,8 +307,8 @@ struct DgradLoader {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 int p, q;
-                bool ok = k < d.K && tap(i, r, s, p, q);
-                ra[i] = ok ? ldf(g + gb[i] + ((long long)p * d.Q + q) * d.K + k) : 0.f;
+                bool ok = k < d.Kg && tap(i, r, s, p, q);
+                ra[i] = ok ? ldf(g + gb[i] + ((long long)p * d.Q + q) * d.K + k0g + k) : 0.f;
             }
         } else {
             int p = 0, q = 0;
@@ -313,21 +316,22 @@ struct DgradLoader {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 int k = k0 + t / 128 + 2 * i;
-                bool ok = okp && k < d.K;
-                ra[i] = ok ? ldf(g + gb[0] + ((long long)k * d.P + p) * d.Q + q) : 0.f;
+                bool ok = okp && k < d.Kg;
+                ra[i] = ok ? ldf(g + gb[0] + ((long long)(k0g + k) * d.P + p) * d.Q + q) : 0.f;
             }
         }
     }
     __device__ void load_b(int kt, float (&rb)[4]) const {
         const int rs = kt / kb, k0 = (kt - rs * kb) * BK;
         const int r = rs / d.S, s = rs - r * d.S;
-        const int c = n0 + t % 64;
+        const int c = n0 + t % 64;  // input channel within the group
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            int k = k0 + t / 64 + 4 * i;
-            bool ok = c < d.C && k < d.K;
-            long long off = NHWC ? (((long long)k * d.R + r) * d.S + s) * d.C + c
-                                 : (((long long)k * d.C + c) * d.R + r) * d.S + s;
+            int kl = k0 + t / 64 + 4 * i;
+            bool ok = c < d.Cg && kl < d.Kg;
+            long long k = k0g + kl;
+            long long off = NHWC ? ((k * d.R + r) * d.S + s) * d.Cg + c
+                                 : ((k * d.Cg + c) * d.R + r) * d.S + s;
             rb[i] = ok ? ldf(w + off) : 0.f;
         }
     }
@@ -343,8 +347,9 @@ struct DgradLoader {
             int n = (int)(rr / d.H);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                int c = n0 + tn * 4 + j;
-                if (c >= d.C) continue;
+                int cl = n0 + tn * 4 + j;
+                if (cl >= d.Cg) continue;
+                const int c = cx0 + cl;
                 long long off = NHWC ? m * d.C + c : (((long long)n * d.C + c) * d.H + h) * d.W + ww;
                 stf(dx + off, acc[i][j]);
             }
@@ -368,13 +373,18 @@ struct WgradLoader {
     float *part;
     int slices, qb, m_tiles;
     int m0, n0, t, r, s, kt0, kt1;
+    int cx0, k0g;  // this group's first input and output channel
 
     __device__ void begin(int tid) {
         t = tid;
         m0 = (blockIdx.x % m_tiles) * BM;
         n0 = (blockIdx.x / m_tiles) * BN;
-        r = blockIdx.z / d.S;
-        s = blockIdx.z - r * d.S;
+        const int RS = d.R * d.S;
+        const int grp = blockIdx.z / RS, tap = blockIdx.z - grp * RS;  // grid layer z = (group, tap)
+        cx0 = grp * d.Cg;
+        k0g = grp * d.Kg;
+        r = tap / d.S;
+        s = tap - r * d.S;
         long long total = (long long)d.N * d.P * qb;
         kt0 = (int)(total * blockIdx.y / slices);
         kt1 = (int)(total * (blockIdx.y + 1) / slices);
@@ -396,8 +406,9 @@ struct WgradLoader {
         for (int i = 0; i < 8; ++i) {
             int kl = A_KFAST ? (t % 16) : (t / 128 + 2 * i);
             int ml = A_KFAST ? (t / 16 + 16 * i) : (t % 128);
-            int q = q0 + kl, k = m0 + ml;
-            bool ok = q < d.Q && k < d.K;
+            int q = q0 + kl, kl2 = m0 + ml;
+            bool ok = q < d.Q && kl2 < d.Kg;
+            const long long k = k0g + kl2;
             long long off = NHWC ? (((long long)n * d.P + p) * d.Q + q) * d.K + k
                                  : (((long long)n * d.K + k) * d.P + p) * d.Q + q;
             ra[i] = ok ? ldf(g + off) : 0.f;
@@ -412,26 +423,28 @@ struct WgradLoader {
         for (int i = 0; i < 4; ++i) {
             int kl = B_KFAST ? (t % 16) : (t / 64 + 4 * i);
             int nl = B_KFAST ? (t / 16 + 16 * i) : (t % 64);
-            int q = q0 + kl, c = n0 + nl;
+            int q = q0 + kl, cl = n0 + nl;
             int ww = q * d.v + s * d.dw - d.pw;
-            bool ok = okh && q < d.Q && c < d.C && ww >= 0 && ww < d.W;
+            bool ok = okh && q < d.Q && cl < d.Cg && ww >= 0 && ww < d.W;
+            const long long c = cx0 + cl;
             long long off = NHWC ? (((long long)n * d.H + h) * d.W + ww) * d.C + c
                                  : (((long long)n * d.C + c) * d.H + h) * d.W + ww;
             rb[i] = ok ? ldf(x + off) : 0.f;
         }
     }
     __device__ void epilogue(const float (&acc)[8][4], int tm, int tn) const {
-        float *out = part + (long long)blockIdx.y * d.K * d.C * d.R * d.S;
+        float *out = part + (long long)blockIdx.y * d.K * d.Cg * d.R * d.S;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            int k = m0 + tm * 8 + i;
-            if (k >= d.K) continue;
+            int kl = m0 + tm * 8 + i;
+            if (kl >= d.Kg) continue;
+            const long long k = k0g + kl;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                int c = n0 + tn * 4 + j;
-                if (c >= d.C) continue;
-                long long off = NHWC ? (((long long)k * d.R + r) * d.S + s) * d.C + c
-                                     : (((long long)k * d.C + c) * d.R + r) * d.S + s;
+                int c = n0 + tn * 4 + j;  // within the group (the filter holds C/G channels)
+                if (c >= d.Cg) continue;
+                long long off = NHWC ? ((k * d.R + r) * d.S + s) * d.Cg + c
+                                     : ((k * d.Cg + c) * d.R + r) * d.S + s;
                 out[off] = acc[i][j];
             }
         }
@@ -468,8 +481,10 @@ template <typename Ti, typename To>
 gbconv_status_t dgrad_typed(const Dims &d, const void *g, const void *w, void *dx,
                             cudaStream_t st) {
     long long M = (long long)d.N * d.H * d.W;
-    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((d.C + BN - 1) / BN), 1);
-    int kb = (d.K + BK - 1) / BK;
+    const int Cg = d.C / d.G, Kg = d.K / d.G;
+    if (d.G > 65535) return GBCONV_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((Cg + BN - 1) / BN), (unsigned)d.G);
+    int kb = (Kg + BK - 1) / BK;
     if (d.layout == GBCONV_NHWC) {
         DgradLoader<Ti, To, true> L{to_k(d), (const Ti *)g, (const Ti *)w, (To *)dx, kb};
         return launch(L, grid, st);
@@ -481,9 +496,11 @@ gbconv_status_t dgrad_typed(const Dims &d, const void *g, const void *w, void *d
 template <typename Ti>
 gbconv_status_t wgrad_typed(const Dims &d, const void *x, const void *g, float *ws, int slices,
                             cudaStream_t st) {
-    int m_tiles = (d.K + BM - 1) / BM, n_tiles = (d.C + BN - 1) / BN;
+    const int Cg = d.C / d.G, Kg = d.K / d.G;
+    int m_tiles = (Kg + BM - 1) / BM, n_tiles = (Cg + BN - 1) / BN;
     int qb = (d.Q + BK - 1) / BK;
-    dim3 grid((unsigned)(m_tiles * n_tiles), (unsigned)slices, (unsigned)(d.R * d.S));
+    if ((long long)d.R * d.S * d.G > 65535) return GBCONV_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)(m_tiles * n_tiles), (unsigned)slices, (unsigned)(d.R * d.S * d.G));
     if (d.layout == GBCONV_NHWC) {
         WgradLoader<Ti, true> L{to_k(d), (const Ti *)x, (const Ti *)g, ws, slices, qb, m_tiles};
         return launch(L, grid, st);

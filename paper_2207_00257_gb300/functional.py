@@ -145,11 +145,12 @@ def workspace(op, prob, device):
     return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device), nbytes
 
 
-def conv2d_dgrad(dy, w, x_shape, stride=1, padding=0, dilation=1, layout="NHWC", out_dtype=None):
+def conv2d_dgrad(dy, w, x_shape, stride=1, padding=0, dilation=1, layout="NHWC", out_dtype=None,
+                 groups=1):
     """dL/dx for upstream gradient dy."""
     _check_dev(dy, w)
     fake_x = torch.empty(x_shape, dtype=dy.dtype, device="meta")
-    prob = make_problem(fake_x, w, stride, padding, dilation, layout, out_dtype)
+    prob = make_problem(fake_x, w, stride, padding, dilation, layout, out_dtype, groups=groups)
     dx = torch.empty(x_shape, dtype=_TORCH[prob.out_dtype], device=dy.device)
     ws, nbytes = workspace(B.GBCONV_OP_DGRAD, prob, dy.device)
     s = B.conv2d_dgrad(prob, dy.data_ptr(), w.data_ptr(), dx.data_ptr(), ws.data_ptr(), nbytes,
@@ -158,11 +159,12 @@ def conv2d_dgrad(dy, w, x_shape, stride=1, padding=0, dilation=1, layout="NHWC",
     return dx
 
 
-def conv2d_wgrad(x, dy, w_shape, stride=1, padding=0, dilation=1, layout="NHWC", with_bias=True):
+def conv2d_wgrad(x, dy, w_shape, stride=1, padding=0, dilation=1, layout="NHWC", with_bias=True,
+                 groups=1):
     """(dL/dw, dL/db) in fp32 for upstream gradient dy."""
     _check_dev(x, dy)
     fake_w = torch.empty(w_shape, dtype=x.dtype, device="meta")
-    prob = make_problem(x, fake_w, stride, padding, dilation, layout)
+    prob = make_problem(x, fake_w, stride, padding, dilation, layout, groups=groups)
     dw = torch.empty(w_shape, dtype=torch.float32, device=x.device)
     db = torch.empty(prob.K, dtype=torch.float32, device=x.device) if with_bias else None
     ws, nbytes = workspace(B.GBCONV_OP_WGRAD, prob, x.device)
@@ -226,16 +228,17 @@ class Conv2dFn(torch.autograd.Function):
     kernels: conv2d_dgrad for dx and conv2d_wgrad for dw, db."""
 
     @staticmethod
-    def forward(ctx, x, w, b, stride, padding, dilation, relu, layout):
-        y = conv2d(x, w, b, stride, padding, dilation, relu, layout)
+    def forward(ctx, x, w, b, stride, padding, dilation, relu, layout, groups=1):
+        y = conv2d(x, w, b, stride, padding, dilation, relu, layout, groups=groups)
         ctx.save_for_backward(x, w, y if relu else None)
-        ctx.conf = (stride, padding, dilation, relu, layout, b is not None, b.dtype if b is not None else None)
+        ctx.conf = (stride, padding, dilation, relu, layout, b is not None,
+                    b.dtype if b is not None else None, groups)
         return y
 
     @staticmethod
     def backward(ctx, gy):
         x, w, y = ctx.saved_tensors
-        stride, padding, dilation, relu, layout, has_b, bdt = ctx.conf
+        stride, padding, dilation, relu, layout, has_b, bdt, groups = ctx.conf
         gy = gy.contiguous()
         if relu:
             # derivative of max(., 0) (and the cast to x's dtype) in the library
@@ -245,14 +248,15 @@ class Conv2dFn(torch.autograd.Function):
         dx = dw = db = None
         if ctx.needs_input_grad[0]:
             dx = conv2d_dgrad(gy, w, tuple(x.shape), stride, padding, dilation, layout,
-                              out_dtype=x.dtype)
+                              out_dtype=x.dtype, groups=groups)
         if ctx.needs_input_grad[1] or (has_b and ctx.needs_input_grad[2]):
             dw32, db32 = conv2d_wgrad(x, gy, tuple(w.shape), stride, padding, dilation, layout,
-                                      with_bias=has_b)
+                                      with_bias=has_b, groups=groups)
             dw = dw32.to(w.dtype)
             db = db32.to(bdt) if has_b else None
-        return dx, dw, db, None, None, None, None, None
+        return dx, dw, db, None, None, None, None, None, None
 
 
-def conv2d_autograd(x, w, b=None, stride=1, padding=0, dilation=1, relu=False, layout="NHWC"):
-    return Conv2dFn.apply(x, w, b, stride, padding, dilation, relu, layout)
+def conv2d_autograd(x, w, b=None, stride=1, padding=0, dilation=1, relu=False, layout="NHWC",
+                    groups=1):
+    return Conv2dFn.apply(x, w, b, stride, padding, dilation, relu, layout, groups)

@@ -221,6 +221,25 @@ def test_quantize_e4m3_matches_oracle():
                           oracle.e4m3_to_f64(codes))
 
 
+@pytest.mark.parametrize("n", [64 * 28 * 28 * 256, 100003, 1 << 16])
+@pytest.mark.parametrize("dt", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+def test_quantize_e4m3_large_tensor_matches_oracle(n, dt):
+    """Per-tensor preparation of large tensors (the FP8 workload's activation,
+    and lengths that are not a multiple of the 8-value vector): scale and
+    every code bit for bit the oracle's."""
+    g = torch.Generator().manual_seed(n % 997)
+    t = (torch.randn(n, generator=g) * 2).clamp_min(0).to(dt)
+    t[7] = -5.0  # the largest magnitude may be negative
+    q, sc = F.quantize_e4m3(t.cuda(), rows=1)
+    F.device_error()
+    codes, scales = oracle.scale_quant_e4m3(t.float().numpy(), 1)
+    assert np.array_equal(sc.cpu().numpy(), scales)
+    got = q.view(torch.uint8).cpu().numpy()
+    assert np.array_equal(oracle.e4m3_to_f64(got), oracle.e4m3_to_f64(codes))
+    nz = oracle.e4m3_to_f64(codes) != 0
+    assert np.array_equal(got[nz], codes[nz])
+
+
 @pytest.mark.parametrize("sh", [ConvShape(2, 32, 9, 9, 32, 3, 3, 1, 1, 1),
                                 ConvShape(3, 128, 10, 10, 64, 3, 3, 1, 1, 1),
                                 ConvShape(2, 144, 8, 8, 40, 1, 1, 1, 0, 1),

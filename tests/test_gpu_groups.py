@@ -153,8 +153,68 @@ def test_groups_argument_checks():
     bad = B.problem(1, 6, 5, 5, 4, 3, 3, groups=4)
     assert B.conv2d_fwd(bad, 16, 32, 0, 0, 0, 64, 0, 0, st) == B.GBCONV_ERR_INVALID_ARG
     p = B.problem(1, 64, 8, 8, 64, 3, 3, 1, 1, 1, groups=64)
-    assert B.conv2d_dgrad(p, 16, 32, 64, 0, 0, st) == B.GBCONV_ERR_UNSUPPORTED
-    assert B.conv2d_wgrad(p, 16, 32, 64, 0, 0, 0, st) == B.GBCONV_ERR_UNSUPPORTED
-    assert B.gbconv_workspace_size(B.GBCONV_OP_DGRAD, p)[0] == B.GBCONV_ERR_UNSUPPORTED
+    assert B.gbconv_workspace_size(B.GBCONV_OP_DGRAD, p) == (B.GBCONV_OK, 0)
+    s, nw = B.gbconv_workspace_size(B.GBCONV_OP_WGRAD, p)
+    assert s == B.GBCONV_OK and nw > 0
+    assert B.conv2d_wgrad(p, 16, 32, 64, 0, 0, 0, st) == B.GBCONV_ERR_WORKSPACE  # none given
     e4 = B.problem(1, 64, 8, 8, 64, 3, 3, 1, 1, 1, B.GBCONV_E4M3, B.GBCONV_BF16, groups=2)
     assert B.conv2d_fwd(e4, 16, 32, 0, 16, 16, 64, 0, 0, st) == B.GBCONV_ERR_UNSUPPORTED
+
+
+# ---- gradients of grouped layers (CUDA cores, one grid layer per group) ----
+
+GRAD_CASES = [  # (N, C, H, W, K, R, stride, pad, G)
+    (2, 16, 9, 9, 16, 3, 1, 1, 16),     # depthwise
+    (2, 16, 9, 8, 32, 3, 2, 1, 16),     # depthwise multiplier 2, stride 2
+    (2, 32, 10, 10, 64, 3, 1, 1, 4),    # 8 -> 16 channels per group
+    (1, 24, 11, 9, 24, 5, 1, 2, 3),     # 5x5, 8 channels per group
+    (2, 128, 8, 8, 128, 3, 1, 1, 32),   # ResNeXt-style 4 channels per group
+]
+
+
+@pytest.mark.parametrize("case", GRAD_CASES, ids=lambda c: "x".join(map(str, c)))
+@pytest.mark.parametrize("layout", ["NHWC", "NCHW"])
+@pytest.mark.parametrize("ind", [torch.float32, torch.bfloat16], ids=["f32", "bf16"])
+def test_grouped_gradients_match_oracle(case, layout, ind):
+    N, C, H, W, K, R, st, pd, G = case
+    if ind == torch.bfloat16 and layout == "NCHW":
+        pytest.skip("BF16 gradients take NHWC")
+    p = oracle.Conv(N, C, H, W, K, R, R, st, pd, 1, layout, groups=G)
+    g = torch.Generator().manual_seed(97 + G)
+    x = torch.randn(p.x_shape, generator=g).to(ind)
+    w = (torch.randn(p.w_shape, generator=g) / np.sqrt(C // G * R * R)).to(ind)
+    gy = torch.randn(p.y_shape, generator=g).to(ind)
+    dx = F.conv2d_dgrad(gy.cuda(), w.cuda(), tuple(x.shape), st, pd, 1, layout,
+                        out_dtype=torch.float32, groups=G)
+    dw, db = F.conv2d_wgrad(x.cuda(), gy.cuda(), tuple(w.shape), st, pd, 1, layout, groups=G)
+    F.device_error()
+    dxr, dxb = oracle.conv2d_dgrad(p, f64(gy), f64(w), with_bound=True)
+    dwr, dwb = oracle.conv2d_wgrad(p, f64(x), f64(gy), with_bound=True)
+    dbr, dbb = oracle.conv2d_bgrad(p, f64(gy), with_bound=True)
+    tol = TOL_F32 if ind == torch.float32 else TOL_ACC32
+    assert oracle.max_normalised_error(f64(dx), dxr, dxb) <= tol
+    assert oracle.max_normalised_error(f64(dw), dwr, dwb) <= tol
+    assert oracle.max_normalised_error(f64(db), dbr, dbb) <= tol
+
+
+def test_grouped_autograd_relu_matches_oracle():
+    """Depthwise layer with ReLU through Conv2dFn (the library masks the
+    gradient, then the grouped data and weight gradients)."""
+    N, C, H, W, G = 2, 16, 8, 8, 16
+    p = oracle.Conv(N, C, H, W, C, 3, 3, 1, 1, 1, "NHWC", groups=G)
+    g = torch.Generator().manual_seed(99)
+    x = torch.randint(-3, 4, p.x_shape, generator=g).float()
+    w = torch.randint(-3, 4, p.w_shape, generator=g).float()
+    b = torch.randint(-4, 4, (C,), generator=g).float() + 0.5
+    gy = torch.randn(p.y_shape, generator=g)
+    xg, wg, bg = (t.cuda().requires_grad_() for t in (x, w, b))
+    y = F.conv2d_autograd(xg, wg, bg, 1, 1, 1, True, "NHWC", groups=G)
+    y.backward(gy.cuda())
+    F.device_error()
+    z = oracle.conv2d_fwd(p, f64(x), f64(w), f64(b))
+    assert np.min(np.abs(z)) >= 0.5
+    gz = oracle.relu_grad(np.maximum(z, 0.0), f64(gy))
+    dxr, dxb = oracle.conv2d_dgrad(p, gz, f64(w), with_bound=True)
+    dwr, dwb = oracle.conv2d_wgrad(p, f64(x), gz, with_bound=True)
+    assert oracle.max_normalised_error(f64(xg.grad), dxr, dxb) <= TOL_F32
+    assert oracle.max_normalised_error(f64(wg.grad), dwr, dwb) <= TOL_F32
