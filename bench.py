@@ -675,15 +675,30 @@ def bench_grouped(torch, dev, args, dist_on, pk):
             s.launch = f
 
     steps = max(3, min(args.steps, 10))
+    # heuristic tile widths, then each problem tuned once (outside the timed
+    # region) as the grouped launch's body, then the tuned grouped launch
+    rh = bench_layers([L(grouped)], steps, 3, 1, torch, dist_on)
+    st = torch.cuda.current_stream().cuda_stream
+    t0 = time.time()
+    widths = []
+    for k, p in enumerate(probs):
+        s_, c = B.gbconv_tune(B.GBCONV_OP_GROUPED, p, xp[k], wp[k], bp[k], yp[k], 0, 0, 3, st)
+        B.check(s_, "gbconv_tune(grouped)")
+        widths.append(c.block_n)
+    tune_s = time.time() - t0
     rg = bench_layers([L(grouped)], steps, 3, 1, torch, dist_on)
     rs = bench_layers([L(separate)], steps, 3, 1, torch, dist_on)
+    B.gbconv_shutdown()  # clears the tuning table again
     del xs, ws, ys
     torch.cuda.empty_cache()
+    tf = lambda r: round(flops / (r["ms_per_step"] * 1e-3) / 1e12, 1)
     return {"problems": len(shapes), "tflop_per_step": round(flops / 1e12, 4),
-            "grouped_ms": round(rg["ms_per_step"], 4),
-            "grouped_tflops": round(flops / (rg["ms_per_step"] * 1e-3) / 1e12, 1),
-            "separate_launches_ms": round(rs["ms_per_step"], 4),
-            "separate_launches_tflops": round(flops / (rs["ms_per_step"] * 1e-3) / 1e12, 1),
+            "grouped_ms": round(rg["ms_per_step"], 4), "grouped_tflops": tf(rg),
+            "grouped_tuning": "per-problem tile width tuned as the grouped launch's body "
+                              f"(gbconv_tune GBCONV_OP_GROUPED, {tune_s:.1f} s for 64 problems)",
+            "tuned_block_n": widths,
+            "heuristic_grouped_ms": round(rh["ms_per_step"], 4), "heuristic_grouped_tflops": tf(rh),
+            "separate_launches_ms": round(rs["ms_per_step"], 4), "separate_launches_tflops": tf(rs),
             "both_in_cuda_graphs": True,
             "frac_of_bf16_peak": round(flops / (rg["ms_per_step"] * 1e-3) / 1e12 / pk["bf16_tflops"], 4)}
 
@@ -810,9 +825,14 @@ def bench_fused(torch, dev, args, dist_on, pk):
 
     steps = max(3, min(args.steps, 20))
     res = bench_layers([L(fused), L(unfused)], steps, 3, 1, torch, dist_on)
+    rb = bench_layers([L(fused)], max(3, min(args.steps, 50)), 1, 1, torch, dist_on)
+    ub = rb["ms_per_step"] * 1e3
+    nbytes = (xb.numel() + wb.numel() + z.numel() + y.numel()) * 2
     f = sh.flops
     return {"workload": "bottleneck_end_" + sh.tag + "_bn_residual_relu",
             "fused_us": round(res["launch_us"][0], 1),
+            "fused_us_back_to_back": round(ub, 2),
+            "fused_frac_of_hbm_back_to_back": round(nbytes / (ub * 1e-6) / 1e9 / pk["hbm_gbs"], 3),
             "fused_tflops": round(f / (res["launch_us"][0] * 1e-6) / 1e12, 1),
             "unfused_conv_plus_torch_elementwise_us": round(res["launch_us"][1], 1),
             "bytes_fused_MB": round((xb.numel() + wb.numel() + z.numel() + y.numel()) * 2 / 1e6, 1)}
@@ -852,11 +872,17 @@ def bench_groups(torch, dev, args, dist_on, pk):
     steps = max(3, min(args.steps, 20))
     res = bench_layers(layers, steps, 3, 1, torch, dist_on)
     out = []
-    for (tag, G, flops, nbytes), us in zip(meta, res["launch_us"]):
-        out.append({"workload": tag, "groups": G, "us": round(us, 1),
-                    "tflops": round(flops / (us * 1e-6) / 1e12, 2),
-                    "gbs": round(nbytes / (us * 1e-6) / 1e9, 1),
-                    "frac_of_hbm": round(nbytes / (us * 1e-6) / 1e9 / pk["hbm_gbs"], 3)})
+    for lay, (tag, G, flops, nbytes), us in zip(layers, meta, res["launch_us"]):
+        # back to back (K launches of this layer alone in one graph, each
+        # overlapping its neighbours' launch and ramp), as the headline layers
+        r1 = bench_layers([lay], max(3, min(args.steps, 50)), 1, 1, torch, dist_on)
+        ub = r1["ms_per_step"] * 1e3
+        out.append({"workload": tag, "groups": G, "us_event_separated": round(us, 1),
+                    "us_back_to_back": round(ub, 2),
+                    "tflops": round(flops / (ub * 1e-6) / 1e12, 2),
+                    "gbs": round(nbytes / (ub * 1e-6) / 1e9, 1),
+                    "frac_of_hbm": round(nbytes / (ub * 1e-6) / 1e9 / pk["hbm_gbs"], 3),
+                    "frac_of_hbm_event_separated": round(nbytes / (us * 1e-6) / 1e9 / pk["hbm_gbs"], 3)})
     return out
 
 

@@ -58,7 +58,14 @@ typedef enum {
 
 typedef enum { GBCONV_F32 = 0, GBCONV_BF16 = 1, GBCONV_E4M3 = 2 } gbconv_dtype_t;
 typedef enum { GBCONV_NCHW = 0, GBCONV_NHWC = 1 } gbconv_layout_t;
-typedef enum { GBCONV_OP_FWD = 0, GBCONV_OP_DGRAD = 1, GBCONV_OP_WGRAD = 2 } gbconv_op_t;
+/* GBCONV_OP_GROUPED: one problem as the body of conv2d_grouped runs it (its
+ * tuning-table entry holds the problem's tile width in the grouped launch). */
+typedef enum {
+    GBCONV_OP_FWD = 0,
+    GBCONV_OP_DGRAD = 1,
+    GBCONV_OP_WGRAD = 2,
+    GBCONV_OP_GROUPED = 3
+} gbconv_op_t;
 
 #define GBCONV_FLAG_BIAS 1u   /* add b[k] (fp32 for F32 output, else fp32 as well) */
 #define GBCONV_FLAG_RELU 2u   /* y = max(y, 0) after the bias */
@@ -298,9 +305,12 @@ gbconv_status_t gbconv_quantize_e4m3(const void *in, int32_t in_dtype, int64_t r
  * (tuned entry if present, else the heuristic); gbconv_set_config stores one.
  * gbconv_tune times every candidate config on the caller's buffers (same
  * arguments as the op: FWD a=x, b=w, out=y; DGRAD a=dy, b=w, out=dx; WGRAD
- * a=x, b=dy, out=dw) with `reps` launches each on `stream`, stores and returns
- * the fastest. The table is keyed by problem, op and device name and can be
- * saved to / loaded from a JSON file (host path). */
+ * a=x, b=dy, out=dw; GROUPED as FWD, timing the grouped launch's body on this
+ * one problem at every tile width, BF16 NHWC only) with `reps` launches each
+ * on `stream`, stores and returns the fastest. The table is keyed by problem,
+ * op and device name and can be saved to / loaded from a JSON file (host
+ * path). conv2d_grouped takes each problem's GROUPED entry when there is one,
+ * else the forward heuristic. */
 gbconv_status_t gbconv_get_config(int32_t op, const gbconv_problem_t *prob, gbconv_config_t *cfg);
 gbconv_status_t gbconv_set_config(int32_t op, const gbconv_problem_t *prob,
                                   const gbconv_config_t *cfg);

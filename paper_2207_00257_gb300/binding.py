@@ -23,7 +23,7 @@ GBCONV_ERR_TIMEOUT = 6
 
 GBCONV_F32, GBCONV_BF16, GBCONV_E4M3 = 0, 1, 2
 GBCONV_NCHW, GBCONV_NHWC = 0, 1
-GBCONV_OP_FWD, GBCONV_OP_DGRAD, GBCONV_OP_WGRAD = 0, 1, 2
+GBCONV_OP_FWD, GBCONV_OP_DGRAD, GBCONV_OP_WGRAD, GBCONV_OP_GROUPED = 0, 1, 2, 3
 GBCONV_FLAG_BIAS, GBCONV_FLAG_RELU = 1, 2
 GBCONV_DEBUG_WAIT_LIMIT_NS, GBCONV_DEBUG_SKIP_LOADS = 1, 2
 GBCONV_ALGO_AUTO, GBCONV_ALGO_IM2COL, GBCONV_ALGO_SHIFT, GBCONV_ALGO_SHIFT_T = 0, 1, 2, 3

@@ -235,6 +235,7 @@ int wgrad_default_slices(const Dims &d) {
 TcConfig config_for(int op, const gbconv_problem_t &p, const Dims &d) {
     TcConfig c{};
     if (tuned(op, p, &c)) return c;
+    if (op == GBCONV_OP_GROUPED) return tc_fwd_default_config(d);  // untuned: the forward heuristic
     if (op == GBCONV_OP_WGRAD) {
         if (d.G == 1 && tc_wgrad_supported(d)) return tc_wgrad_default_config(d);
         c.split_k = wgrad_default_slices(d);
@@ -486,6 +487,7 @@ gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, 
         *bytes = wgrad_ws_bytes(d, std::max(1, c.split_k));
         return GBCONV_OK;
     }
+    if (op == GBCONV_OP_GROUPED) return GBCONV_OK;  // no workspace
     return GBCONV_ERR_INVALID_ARG;
 }
 
@@ -622,7 +624,7 @@ gbconv_status_t conv2d_grouped(int32_t count, const gbconv_problem_t *probs, con
         if ((d[i].flags & GBCONV_FLAG_BIAS) && !b[i]) return GBCONV_ERR_INVALID_ARG;
         s = check_tc_fwd(d[i], x[i], w[i], y[i]);
         if (s != GBCONV_OK) return s;
-        cfg[i] = config_for(GBCONV_OP_FWD, probs[i], d[i]);
+        cfg[i] = config_for(GBCONV_OP_GROUPED, probs[i], d[i]);
     }
     if (make_guard().err == nullptr) return GBCONV_ERR_CUDA;
     return launch_tc_grouped(count, d.data(), cfg.data(), x, w, b.data(), y,
@@ -663,7 +665,7 @@ gbconv_status_t gbconv_get_config(int32_t op, const gbconv_problem_t *prob, gbco
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
-    if (!cfg || op < GBCONV_OP_FWD || op > GBCONV_OP_WGRAD) return GBCONV_ERR_INVALID_ARG;
+    if (!cfg || op < GBCONV_OP_FWD || op > GBCONV_OP_GROUPED) return GBCONV_ERR_INVALID_ARG;
     TcConfig c = config_for(op, *prob, d);
     cfg->block_n = c.block_n;
     cfg->stages = c.stages;
@@ -678,7 +680,7 @@ gbconv_status_t gbconv_set_config(int32_t op, const gbconv_problem_t *prob,
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
-    if (!cfg || op < GBCONV_OP_FWD || op > GBCONV_OP_WGRAD) return GBCONV_ERR_INVALID_ARG;
+    if (!cfg || op < GBCONV_OP_FWD || op > GBCONV_OP_GROUPED) return GBCONV_ERR_INVALID_ARG;
     if (cfg->block_n && cfg->block_n != 32 && cfg->block_n != 64 && cfg->block_n != 128 &&
         cfg->block_n != 256)
         return GBCONV_ERR_INVALID_ARG;
@@ -703,7 +705,7 @@ gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void
     Dims d;
     gbconv_status_t s = make_dims(prob, &d);
     if (s != GBCONV_OK) return s;
-    if (!a || !b || !out || op < GBCONV_OP_FWD || op > GBCONV_OP_WGRAD) return GBCONV_ERR_INVALID_ARG;
+    if (!a || !b || !out || op < GBCONV_OP_FWD || op > GBCONV_OP_GROUPED) return GBCONV_ERR_INVALID_ARG;
     if (d.G > 1) return GBCONV_ERR_UNSUPPORTED;  // grouped layers have no tunable configuration
     if (reps < 1) reps = 1;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -714,6 +716,18 @@ gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void
             TcConfig c = base;
             c.split_k = sk;
             if (wgrad_ws_bytes(d, sk) <= ws_bytes) cands.push_back(c);
+        }
+    } else if (op == GBCONV_OP_GROUPED) {
+        // the grouped launch's body (the im2col kernel): its per-problem tile width
+        if (d.in_dtype != GBCONV_BF16 || d.out_dtype != GBCONV_BF16 || d.layout != GBCONV_NHWC ||
+            check_tc_fwd(d, a, b, out) != GBCONV_OK)
+            return GBCONV_ERR_UNSUPPORTED;
+        for (int bn : {32, 64, 128, 256}) {
+            if (bn > 32 && bn / 2 >= d.K) continue;
+            TcConfig c = base;
+            c.block_n = bn;
+            c.algo = GBCONV_ALGO_IM2COL;
+            cands.push_back(c);
         }
     } else {
         Dims t = d;
@@ -775,6 +789,12 @@ gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void
         auto run = [&]() -> gbconv_status_t {
             if (op == GBCONV_OP_FWD) return do_fwd(d, c, a, b, bias, nullptr, nullptr, out, st);
             if (op == GBCONV_OP_DGRAD) return do_dgrad(d, c, a, b, out, ws, ws_bytes, st);
+            if (op == GBCONV_OP_GROUPED) {
+                const void *xa[1] = {a}, *wb[1] = {b};
+                const float *bb[1] = {(d.flags & GBCONV_FLAG_BIAS) ? bias : nullptr};
+                void *ya[1] = {out};
+                return launch_tc_grouped(1, &d, &c, xa, wb, bb, ya, st);
+            }
             return do_wgrad(d, c, a, b, static_cast<float *>(out), nullptr, ws, ws_bytes, st);
         };
         if (run() != GBCONV_OK) continue;  // warm-up; skips configs that do not apply

@@ -116,3 +116,29 @@ def test_grouped_workload_64_problems_graph():
     torch.cuda.synchronize()
     F.device_error()
     _check(shapes, xs, ws, bs, masters, ys, relu=True, max_points=4096, full_below_flops=1e9)
+
+
+def test_grouped_tuned_tile_widths_match_oracle():
+    """Each problem tuned as the grouped launch's body (gbconv_tune with
+    GBCONV_OP_GROUPED) stores one of the candidate tile widths; the grouped
+    launch then runs with the stored widths and still matches the oracle."""
+    xs, ws, bs, masters = _inputs(SMALL, 620)
+    ys = [torch.empty(s.y_shape(), dtype=torch.bfloat16, device="cuda") for s in SMALL]
+    st = torch.cuda.current_stream().cuda_stream
+    try:
+        for i, sh in enumerate(SMALL):
+            prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, 1,
+                             B.GBCONV_BF16, B.GBCONV_BF16, B.GBCONV_NHWC,
+                             B.GBCONV_FLAG_BIAS | B.GBCONV_FLAG_RELU)
+            s, c = B.gbconv_tune(B.GBCONV_OP_GROUPED, prob, xs[i].data_ptr(), ws[i].data_ptr(),
+                                 bs[i].data_ptr(), ys[i].data_ptr(), 0, 0, 2, st)
+            B.check(s, "gbconv_tune")
+            assert c.block_n in (32, 64, 128, 256)
+            s, c2 = B.gbconv_get_config(B.GBCONV_OP_GROUPED, prob)
+            assert s == B.GBCONV_OK and c2.block_n == c.block_n
+        out = F.conv2d_grouped(xs, ws, bs, [s.stride for s in SMALL], [s.pad for s in SMALL],
+                               relu=True)
+        F.device_error()
+    finally:
+        B.gbconv_shutdown()
+    _check(SMALL, xs, ws, bs, masters, out, relu=True)
