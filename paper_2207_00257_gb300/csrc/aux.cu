@@ -35,7 +35,15 @@ __global__ void reduce_slices_kernel(const float *__restrict__ ws, int slices, l
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         float sum = 0.f, comp = 0.f;
-        for (int s = 0; s < slices; ++s) neumaier(sum, comp, ws[(long long)s * n + i]);
+        int s = 0;
+        for (; s + 8 <= slices; s += 8) {  // eight loads in flight, summed in slice order
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = ws[(long long)(s + j) * n + i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) neumaier(sum, comp, v[j]);
+        }
+        for (; s < slices; ++s) neumaier(sum, comp, ws[(long long)s * n + i]);
         out[i] = sum + comp;
     }
 }

@@ -80,6 +80,7 @@ gbconv_status_t launch_simt_wgrad_partials(const Dims &d, const void *x, const v
 // aux.cu
 gbconv_status_t launch_reduce_slices(const float *ws, int slices, long long n, float *out,
                                      cudaStream_t st);
+
 gbconv_status_t launch_bias_grad(const Dims &d, const void *g, float *db, float *ws,
                                  int slices, cudaStream_t st);
 gbconv_status_t launch_rotate_filter(const Dims &d, const void *w, void *w_rot, cudaStream_t st);

@@ -361,7 +361,10 @@ gbconv_status_t launch_tc_wgrad_partials(const Dims &d, const TcConfig &cfg_in, 
     const long long nblocks = (d.M() + PIX - 1) / PIX;
     int slices = std::max(1, cfg.split_k);
     if (slices > nblocks) return GBCONV_ERR_INVALID_ARG;  // every slice needs pixels
-    int stages = cfg.stages >= 2 && cfg.stages <= max_stages(bn) ? cfg.stages : max_stages(bn);
+    // Step `it` is issued by producer warp it % NPROD after its wait on the
+    // ring slot's previous use; with fewer slots than producer warps that
+    // parity wait could refer to a use two back. Hence stages >= NPROD.
+    int stages = cfg.stages >= NPROD && cfg.stages <= max_stages(bn) ? cfg.stages : max_stages(bn);
     WgParams prm;
     memset(&prm, 0, sizeof(prm));
     // dy as [M][K]
