@@ -764,13 +764,40 @@ def bench_backward(torch, dev, args, dist_on, pk):
         B.check(B.gbconv_set_config(B.GBCONV_OP_DGRAD, prob2,
                                     B.gbconv_config_t(0, 0, 0, 0, B.GBCONV_ALGO_AUTO)), "set_config")
     cc_us = res_cc["launch_us"][0]
+    # the weight gradient on the band kernel (one unit per filter row: dy and
+    # one x band per row, a third of the per-tap kernel's shared-memory ingest)
+    split_tap = B.gbconv_get_config(B.GBCONV_OP_WGRAD, prob)[1].split_k
+    B.check(B.gbconv_set_config(B.GBCONV_OP_WGRAD, prob,
+                                B.gbconv_config_t(0, 0, 0, 0, B.GBCONV_ALGO_SHIFT)), "set_config")
+    try:
+        _, nwb = B.gbconv_workspace_size(B.GBCONV_OP_WGRAD, prob)
+        wsb = torch.empty(max(nwb, 1), dtype=torch.uint8, device=dev)
+
+        def wgrad_band(i, stream):
+            B.check(B.conv2d_wgrad(prob, xb.data_ptr(), gb.data_ptr(), dw.data_ptr(), db.data_ptr(),
+                                   wsb.data_ptr(), nwb, stream), "wgrad band")
+        res_band = bench_layers([L(wgrad_band)], steps, 3, 1, torch, dist_on)
+        split_band = B.gbconv_get_config(B.GBCONV_OP_WGRAD, prob)[1].split_k
+    finally:
+        B.gbconv_shutdown()  # back to the default weight-gradient config
+        del wsb
+    band_us = res_band["launch_us"][0]
+    # algorithmic shared-memory ingest of the two kernels (dy and x, BF16):
+    # per tap (R*S = 9 loads of each) vs per filter row (3 loads of each, over
+    # Wx = 57 positions per 56-wide row)
+    m_bytes = sh.N * sh.H * sh.W * sh.C * 2
     f = sh.flops
     f2 = s2.flops
     return {"workload": sh.tag, "dgrad_us": round(res["launch_us"][0], 1),
             "wgrad_us": round(res["launch_us"][1], 1),
             "dgrad_tflops": round(f / (res["launch_us"][0] * 1e-6) / 1e12, 1),
             "wgrad_tflops": round(f / (res["launch_us"][1] * 1e-6) / 1e12, 1),
-            "wgrad_split_k": B.gbconv_get_config(B.GBCONV_OP_WGRAD, prob)[1].split_k,
+            "wgrad_split_k": split_tap,
+            "wgrad_band": {"us": round(band_us, 1),
+                           "tflops": round(f / (band_us * 1e-6) / 1e12, 1),
+                           "split_k": split_band,
+                           "smem_ingest_mb": round(3 * 2 * m_bytes * 57 / 56 / 1e6, 1),
+                           "per_tap_smem_ingest_mb": round(9 * 2 * m_bytes / 1e6, 1)},
             "dgrad_stride2": {"workload": "dgrad_" + s2.tag,
                               "subpixel_tc_us": round(res["launch_us"][2], 1),
                               "subpixel_tc_tflops": round(f2 / (res["launch_us"][2] * 1e-6) / 1e12, 1),

@@ -124,8 +124,13 @@ typedef struct {
  * output pixels on the MMA's M, one input band per stride phase and channel
  * block, the filter resident in shared memory, one SM per 128-position tile)
  * or GBCONV_ALGO_PBAND_PAIR (the same on pairs of SMs: one 256-row MMA per
- * pair, each SM holding half of the filter). A zero field means "library
- * default". */
+ * pair, each SM holding half of the filter). For the weight gradient (BF16
+ * NHWC, C % 64 == 0): GBCONV_ALGO_AUTO / GBCONV_ALGO_IM2COL (one work unit per
+ * filter tap, dy and an im2col tile of x loaded per tap), GBCONV_ALGO_SHIFT
+ * (stride 1, multi-tap: one unit per filter row, dy and one x band loaded per
+ * row and the row's taps read as shifts of the band, a third of the
+ * shared-memory ingest for 3x3 layers) or GBCONV_ALGO_SIMT (CUDA cores). A
+ * zero field means "library default". */
 #define GBCONV_ALGO_AUTO 0
 #define GBCONV_ALGO_IM2COL 1
 #define GBCONV_ALGO_SHIFT 2

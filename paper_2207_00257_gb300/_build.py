@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbconv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["api.cu", "simt.cu", "simt_fast.cu", "aux.cu", "tc_fwd.cu", "tc_fwd_shift.cu", "tc_fwd_t.cu", "tc_fwd_p.cu", "tc_wgrad.cu", "tmap.cu", "depthwise.cu", "nll.cu"]
+UNITS = ["api.cu", "simt.cu", "simt_fast.cu", "aux.cu", "tc_fwd.cu", "tc_fwd_shift.cu", "tc_fwd_t.cu", "tc_fwd_p.cu", "tc_wgrad.cu", "tc_wgrad_shift.cu", "tmap.cu", "depthwise.cu", "nll.cu"]
 
 
 def _nvcc() -> str:

@@ -404,10 +404,16 @@ gbconv_status_t do_wgrad(const Dims &d, const TcConfig &cfg, const void *x, cons
                          float *dw, float *db, void *ws, size_t ws_bytes, cudaStream_t st) {
     if (d.in_dtype == GBCONV_E4M3) return GBCONV_ERR_UNSUPPORTED;
     const long long kcrs = (long long)d.K * (d.C / d.G) * d.R * d.S;  // the filter holds C/G channels
-    const bool tc = d.G == 1 && tc_wgrad_supported(d) && aligned16(x) && aligned16(dy) && aligned16(ws);
-    int slices = std::max(1, cfg.split_k);
+    // tensor-core kernels: the per-tap im2col kernel (algo AUTO / IM2COL) or,
+    // on request (algo SHIFT), the band kernel; GBCONV_ALGO_SIMT asks for the
+    // CUDA-core kernel
+    const bool al = aligned16(x) && aligned16(dy) && aligned16(ws);
+    const bool band = d.G == 1 && al && cfg.algo == GBCONV_ALGO_SHIFT && tc_wgrad_shift_supported(d);
+    const bool tc = !band && d.G == 1 && al && cfg.algo != GBCONV_ALGO_SIMT && tc_wgrad_supported(d);
+    int slices = cfg.split_k > 0 ? cfg.split_k : (band ? tc_wgrad_shift_default_slices(d) : 1);
     if (slices > 1024) return GBCONV_ERR_INVALID_ARG;
-    // the tensor-core kernel gives every slice at least one 64-pixel step
+    // the tensor-core kernels give every slice at least one reduction step
+    if (band) slices = (int)std::max<long long>(1, std::min<long long>(slices, tc_wgrad_shift_bands(d)));
     if (tc) slices = (int)std::max<long long>(1, std::min<long long>(slices, tc_wgrad_pixel_steps(d)));
     size_t need = wgrad_ws_bytes(d, slices);
     if (!ws || ws_bytes < need) return GBCONV_ERR_WORKSPACE;
@@ -419,7 +425,9 @@ gbconv_status_t do_wgrad(const Dims &d, const TcConfig &cfg, const void *x, cons
         return cuda_status(e);
     }
     gbconv_status_t s;
-    if (tc) {
+    if (band) {
+        s = launch_tc_wgrad_shift_partials(d, slices, x, dy, part, st);
+    } else if (tc) {
         TcConfig c = cfg;
         c.split_k = slices;
         s = launch_tc_wgrad_partials(d, c, x, dy, part, st);
@@ -691,6 +699,9 @@ gbconv_status_t gbconv_set_config(int32_t op, const gbconv_problem_t *prob,
     if (cfg->block_n) c.block_n = cfg->block_n;
     if (cfg->stages) c.stages = cfg->stages;
     if (cfg->split_k) c.split_k = cfg->split_k;
+    // the band weight-gradient kernel's own default slice count
+    else if (op == GBCONV_OP_WGRAD && cfg->algo == GBCONV_ALGO_SHIFT && tc_wgrad_shift_supported(d))
+        c.split_k = tc_wgrad_shift_default_slices(d);
     c.raster = cfg->raster;
     c.algo = cfg->algo;
     std::string k = problem_key(op, *prob);
@@ -712,10 +723,24 @@ gbconv_status_t gbconv_tune(int32_t op, const gbconv_problem_t *prob, const void
     const TcConfig base = config_for(op, *prob, d);
     std::vector<TcConfig> cands;
     if (op == GBCONV_OP_WGRAD) {
-        for (int sk : {1, 2, 4, 8, 16, 32, 64}) {
-            TcConfig c = base;
-            c.split_k = sk;
-            if (wgrad_ws_bytes(d, sk) <= ws_bytes) cands.push_back(c);
+        // the per-tap kernel and the band kernel, each at a range of slice
+        // counts including its default
+        std::vector<int> algos;
+        if (tc_wgrad_supported(d)) algos.push_back(GBCONV_ALGO_IM2COL);
+        if (tc_wgrad_shift_supported(d)) algos.push_back(GBCONV_ALGO_SHIFT);
+        if (algos.empty()) algos.push_back(base.algo);
+        for (int algo : algos) {
+            std::vector<int> splits = {1, 2, 4, 8, 16, 32, 64};
+            if (algo == GBCONV_ALGO_SHIFT) splits.push_back(tc_wgrad_shift_default_slices(d));
+            if (algo == GBCONV_ALGO_IM2COL) splits.push_back(tc_wgrad_default_config(d).split_k);
+            std::sort(splits.begin(), splits.end());
+            splits.erase(std::unique(splits.begin(), splits.end()), splits.end());
+            for (int sk : splits) {
+                TcConfig c = base;
+                c.algo = algo;
+                c.split_k = sk;
+                if (wgrad_ws_bytes(d, sk) <= ws_bytes) cands.push_back(c);
+            }
         }
     } else if (op == GBCONV_OP_GROUPED) {
         // the grouped launch's body (the im2col kernel): its per-problem tile width

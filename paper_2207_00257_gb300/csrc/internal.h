@@ -80,7 +80,6 @@ gbconv_status_t launch_simt_wgrad_partials(const Dims &d, const void *x, const v
 // aux.cu
 gbconv_status_t launch_reduce_slices(const float *ws, int slices, long long n, float *out,
                                      cudaStream_t st);
-
 gbconv_status_t launch_bias_grad(const Dims &d, const void *g, float *db, float *ws,
                                  int slices, cudaStream_t st);
 gbconv_status_t launch_rotate_filter(const Dims &d, const void *w, void *w_rot, cudaStream_t st);
@@ -148,6 +147,13 @@ long long tc_wgrad_pixel_steps(const Dims &d);  // 64-pixel reduction steps
 TcConfig tc_wgrad_default_config(const Dims &d);
 gbconv_status_t launch_tc_wgrad_partials(const Dims &d, const TcConfig &cfg, const void *x,
                                          const void *g, float *ws, cudaStream_t st);
+// tc_wgrad_shift.cu: stride-1 multi-tap layers, the taps of one filter row as
+// row shifts of one input band (reduction steps = bands of output rows).
+bool tc_wgrad_shift_supported(const Dims &d);
+long long tc_wgrad_shift_bands(const Dims &d);
+int tc_wgrad_shift_default_slices(const Dims &d);
+gbconv_status_t launch_tc_wgrad_shift_partials(const Dims &d, int slices, const void *x,
+                                               const void *g, float *ws, cudaStream_t st);
 
 // tmap.cpp: tensor-map encoding through the driver entry points.
 gbconv_status_t encode_im2col_act(CUtensorMap *m, const Dims &d, const void *x, int elem_bytes,

@@ -374,3 +374,94 @@ def test_tc_wgrad_integer_exact():
     p = oconv(sh)
     assert np.array_equal(f64(dw), oracle.conv2d_wgrad(p, f64(x), f64(g)))
     assert np.array_equal(f64(db), oracle.conv2d_bgrad(p, f64(g)))
+
+
+# ---- the two tensor-core weight-gradient kernels, forced in turn ----
+
+BAND_WGRAD_SHAPES = [
+    ConvShape(2, 64, 9, 11, 64, 3, 3, 1, 1, 1),
+    ConvShape(1, 64, 15, 13, 200, 3, 3, 1, 2, 2),      # dilation 2, two output-channel tiles
+    ConvShape(2, 192, 10, 10, 32, 5, 5, 1, 2, 1),      # 5x5, three 64-channel input tiles
+    ConvShape(1, 64, 5, 5, 16, 3, 3, 1, 1, 1),         # fewer positions than one band
+    ConvShape(1, 64, 9, 10, 64, 3, 3, 1, 1, 2),        # pad < (S-1)*dil: row width Q + 3
+    ConvShape(1, 64, 9, 10, 40, 3, 3, 1, (1, 0), 1),   # no column padding: no wrap
+    ConvShape(1, 64, 9, 10, 64, 3, 3, 1, (0, 2), 1),   # column padding 2
+    ConvShape(2, 128, 5, 70, 136, 3, 3, 1, 1, 1),      # ragged second output-channel tile
+    ConvShape(1, 256, 6, 6, 64, 3, 3, 1, 1, 1),        # two 128-channel input tiles
+    ConvShape(1, 64, 4, 4, 8, 2, 2, 1, 0, 1),          # 2x2, K = 8
+    ConvShape(1, 64, 6, 20, 64, 1, 7, 1, 3, 1),        # 1x7
+    ConvShape(1, 128, 7, 6, 64, 5, 3, 1, 3, 1),        # 5x3, pad 3
+]
+
+
+def _wgrad_err(sh, seed, algo, split=0):
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, sh.stride, sh.pad, sh.dil,
+                     B.GBCONV_BF16, B.GBCONV_BF16)
+    B.check(B.gbconv_set_config(B.GBCONV_OP_WGRAD, prob, B.gbconv_config_t(0, 0, split, 0, algo)),
+            "set_config")
+    try:
+        x, _, _, g = make_inputs(sh, seed, grad=True)
+        xb, gb = x.bfloat16(), g.bfloat16()
+        dw, db = F.conv2d_wgrad(xb.cuda(), gb.cuda(), (sh.K, sh.R, sh.S, sh.C), sh.stride, sh.pad,
+                                sh.dil)
+        F.device_error()
+    finally:
+        B.gbconv_shutdown()
+    p = oconv(sh)
+    dwr, dwb = oracle.conv2d_wgrad(p, f64(xb), f64(gb), with_bound=True)
+    dbr, dbb = oracle.conv2d_bgrad(p, f64(gb), with_bound=True)
+    return (oracle.max_normalised_error(f64(dw).reshape(-1), dwr.reshape(-1), dwb.reshape(-1)),
+            oracle.max_normalised_error(f64(db), dbr, dbb))
+
+
+@pytest.mark.parametrize("algo", ["band", "im2col"])
+@pytest.mark.parametrize("sh", BAND_WGRAD_SHAPES, ids=_id)
+def test_wgrad_band_and_per_tap_kernels(sh, algo):
+    a = B.GBCONV_ALGO_SHIFT if algo == "band" else B.GBCONV_ALGO_IM2COL
+    for split in (0, 3):
+        ew, eb = _wgrad_err(sh, 64, a, split)
+        assert ew <= TOL_ACC32 and eb <= TOL_ACC32, (split, ew, eb)
+
+
+@pytest.mark.parametrize("algo", ["band", "im2col"])
+def test_wgrad_kernels_integer_exact(algo):
+    """Integer x and g on both tensor-core kernels, ragged bands and tiles."""
+    sh = ConvShape(3, 128, 11, 13, 72, 3, 3, 1, 1, 1)
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, 1, 1, 1, B.GBCONV_BF16,
+                     B.GBCONV_BF16)
+    a = B.GBCONV_ALGO_SHIFT if algo == "band" else B.GBCONV_ALGO_IM2COL
+    B.check(B.gbconv_set_config(B.GBCONV_OP_WGRAD, prob, B.gbconv_config_t(0, 0, 7, 0, a)),
+            "set_config")
+    try:
+        x, w, _, g = make_inputs(sh, 65, x_dist=("int", -4, 4), w_dist=("int", -4, 4), grad=True)
+        g = torch.randint(-4, 5, g.shape, generator=torch.Generator().manual_seed(66)).float()
+        dw, db = F.conv2d_wgrad(x.bfloat16().cuda(), g.bfloat16().cuda(), tuple(w.shape), 1, 1, 1)
+        F.device_error()
+    finally:
+        B.gbconv_shutdown()
+    p = oconv(sh)
+    assert np.array_equal(f64(dw), oracle.conv2d_wgrad(p, f64(x), f64(g)))
+    assert np.array_equal(f64(db), oracle.conv2d_bgrad(p, f64(g)))
+
+
+def test_wgrad_band_full_size_sampled():
+    """The band kernel on the backward workload (N=32, C=K=128, 56x56, 3x3) at
+    its default slice count: 4096 sampled weights and every bias."""
+    sh = config_backward()
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, 1, 1, 1, B.GBCONV_BF16,
+                     B.GBCONV_BF16)
+    B.check(B.gbconv_set_config(B.GBCONV_OP_WGRAD, prob,
+                                B.gbconv_config_t(0, 0, 0, 0, B.GBCONV_ALGO_SHIFT)), "set_config")
+    try:
+        x, _, _, g = make_inputs(sh, 67, grad=True)
+        xb, gb = x.bfloat16(), g.bfloat16()
+        dw, db = F.conv2d_wgrad(xb.cuda(), gb.cuda(), (sh.K, sh.R, sh.S, sh.C), 1, 1, 1)
+        F.device_error()
+    finally:
+        B.gbconv_shutdown()
+    p = oconv(sh)
+    idx = np.random.default_rng(68).choice(sh.K * sh.R * sh.S * sh.C, 4096, replace=False)
+    dwr, dwb = oracle.conv2d_wgrad(p, f64(xb), f64(gb), idx=idx, with_bound=True)
+    assert oracle.max_normalised_error(f64(dw).reshape(-1)[idx], dwr, dwb) <= TOL_ACC32
+    dbr, dbb = oracle.conv2d_bgrad(p, f64(gb), with_bound=True)
+    assert oracle.max_normalised_error(f64(db), dbr, dbb) <= TOL_ACC32

@@ -67,24 +67,33 @@ def test_staged_depthwise_wait_timeout_reported():
     assert torch.equal(y, ref)
 
 
-def test_wgrad_wait_timeout_reported():
-    """Tensor-core weight gradient: no loads issued -> the MMA and epilogue
-    waits run out, the timeout is recorded, TMEM is freed, and the next call
-    gives the same gradients as before."""
+@pytest.mark.parametrize("algo", ["im2col", "band"])
+def test_wgrad_wait_timeout_reported(algo):
+    """Both tensor-core weight-gradient kernels: no loads issued -> the MMA
+    and epilogue waits run out, the timeout is recorded, TMEM is freed, and
+    the next call gives the same gradients as before."""
     sh = ConvShape(2, 64, 9, 9, 64, 3, 3, 1, 1, 1)
     x, w, _, g = make_inputs(sh, 42, grad=True)
     xb, gb = x.bfloat16().cuda(), g.bfloat16().cuda()
-    ref = F.conv2d_wgrad(xb, gb, tuple(w.shape), 1, 1, 1)
-    F.device_error()
-    B.check(B.gbconv_debug_set(B.GBCONV_DEBUG_WAIT_LIMIT_NS, 20_000_000), "debug")  # 20 ms
-    B.check(B.gbconv_debug_set(B.GBCONV_DEBUG_SKIP_LOADS, 1), "debug")
+    prob = B.problem(sh.N, sh.C, sh.H, sh.W, sh.K, sh.R, sh.S, 1, 1, 1, B.GBCONV_BF16,
+                     B.GBCONV_BF16)
+    a = B.GBCONV_ALGO_SHIFT if algo == "band" else B.GBCONV_ALGO_IM2COL
+    B.check(B.gbconv_set_config(B.GBCONV_OP_WGRAD, prob, B.gbconv_config_t(0, 0, 4, 0, a)),
+            "set_config")
     try:
-        F.conv2d_wgrad(xb, gb, tuple(w.shape), 1, 1, 1)
-        st = B.gbconv_get_device_error(torch.cuda.current_stream().cuda_stream)
-        assert st == B.GBCONV_ERR_TIMEOUT
+        ref = F.conv2d_wgrad(xb, gb, tuple(w.shape), 1, 1, 1)
+        F.device_error()
+        B.check(B.gbconv_debug_set(B.GBCONV_DEBUG_WAIT_LIMIT_NS, 20_000_000), "debug")  # 20 ms
+        B.check(B.gbconv_debug_set(B.GBCONV_DEBUG_SKIP_LOADS, 1), "debug")
+        try:
+            F.conv2d_wgrad(xb, gb, tuple(w.shape), 1, 1, 1)
+            st = B.gbconv_get_device_error(torch.cuda.current_stream().cuda_stream)
+            assert st == B.GBCONV_ERR_TIMEOUT
+        finally:
+            B.gbconv_debug_set(B.GBCONV_DEBUG_SKIP_LOADS, 0)
+            B.gbconv_debug_set(B.GBCONV_DEBUG_WAIT_LIMIT_NS, 0)
+        dw, db = F.conv2d_wgrad(xb, gb, tuple(w.shape), 1, 1, 1)
+        F.device_error()
+        assert torch.equal(dw, ref[0]) and torch.equal(db, ref[1])
     finally:
-        B.gbconv_debug_set(B.GBCONV_DEBUG_SKIP_LOADS, 0)
-        B.gbconv_debug_set(B.GBCONV_DEBUG_WAIT_LIMIT_NS, 0)
-    dw, db = F.conv2d_wgrad(xb, gb, tuple(w.shape), 1, 1, 1)
-    F.device_error()
-    assert torch.equal(dw, ref[0]) and torch.equal(db, ref[1])
+        B.gbconv_shutdown()
