@@ -312,8 +312,19 @@ __global__ void amax_kernel(const T *__restrict__ in, long long len, unsigned *_
     const T *g = in + (long long)blockIdx.y * len;
     float m = 0.f;
     if (VEC) {
-        for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 8; i < len;
-             i += (long long)gridDim.x * blockDim.x * 8) {
+        constexpr int U = 4;  // four 8-element steps in flight per thread
+        const long long stride = (long long)gridDim.x * blockDim.x * 8;
+        long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 8;
+        for (; i + (U - 1) * stride < len; i += U * stride) {
+            float v[U][8];
+#pragma unroll
+            for (int u = 0; u < U; ++u) load8(g + i + u * stride, v[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) m = fmaxf(m, fabsf(v[u][k]));
+        }
+        for (; i < len; i += stride) {
             float v[8];
             load8(g + i, v);
 #pragma unroll
@@ -338,8 +349,36 @@ __device__ __forceinline__ float scale_of(unsigned amax_bits) {
     return (s >= 1.0e-12f) ? s : 1.0e-12f;
 }
 
-__device__ __forceinline__ uint8_t e4m3_of(float v, float s) {
-    return (uint8_t)__nv_cvt_float_to_fp8(__fdiv_rn(v, s), __NV_SATFINITE, __NV_E4M3);
+// v / s rounded to nearest even in binary32, for a normal s > 0 and its
+// correctly rounded reciprocal r, by multiplication and exact remainders:
+//  1. q0 = v*r, then one Markstein refinement q1 = q0 + (v - s*q0)*r (both
+//     fused), which leaves q1 a faithful rounding of v/s;
+//  2. for a faithful q1 the remainder e = v - s*q1 is exactly representable
+//     (Boldo and Daumas, representable correcting terms), so one more fused
+//     step gives it exactly;
+//  3. v/s lies between q1 and its neighbour q2 on e's side; it passes their
+//     midpoint iff |e| > s*|q2 - q1|/2, where the right side is exact (a power
+//     of two times s). Equality is a tie: the even significand wins.
+// Exactness needs s*|q2 - q1|/2 normal: every quotient at or above 2^-10 in
+// magnitude (where E4M3 rounding decisions happen, s >= 1e-12) has it; below,
+// q may differ from the rounded quotient, but both round to E4M3 zero.
+__device__ __forceinline__ float div_rn_by_recip(float v, float s, float r) {
+    const float q0 = v * r;
+    const float q1 = fmaf(fmaf(-q0, s, v), r, q0);
+    const float e = fmaf(-q1, s, v);
+    if (e == 0.f || q1 == 0.f || !isfinite(q1)) return q1;
+    // neighbour of q1 towards the exact quotient (e and q1 of equal sign: away from zero)
+    const int step = (e > 0.f) == (q1 > 0.f) ? 1 : -1;
+    const float q2 = __int_as_float(__float_as_int(q1) + step);
+    const float half = s * (fabsf(q2 - q1) * 0.5f);
+    const float ae = fabsf(e);
+    if (ae < half) return q1;
+    if (ae > half) return q2;
+    return (__float_as_int(q1) & 1) ? q2 : q1;
+}
+
+__device__ __forceinline__ uint8_t e4m3_of(float v, float s, float r) {
+    return (uint8_t)__nv_cvt_float_to_fp8(div_rn_by_recip(v, s, r), __NV_SATFINITE, __NV_E4M3);
 }
 
 template <typename T, bool VEC>
@@ -349,23 +388,43 @@ __global__ void quant_kernel(const T *__restrict__ in, long long len,
     if (threadIdx.x == 0) ptx::griddep_launch();
     const long long base = (long long)blockIdx.y * len;
     const float s = scale_of(amax_bits[blockIdx.y]);
+    const float r = __frcp_rn(s);
     if (VEC) {
-        for (long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 8; i < len;
-             i += (long long)gridDim.x * blockDim.x * 8) {
+        // four 8-element steps per trip, all loads issued before the divisions,
+        // so that the memory latency overlaps the arithmetic
+        constexpr int U = 4;
+        const long long stride = (long long)gridDim.x * blockDim.x * 8;
+        long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 8;
+        for (; i + (U - 1) * stride < len; i += U * stride) {
+            float v[U][8];
+#pragma unroll
+            for (int u = 0; u < U; ++u) load8(in + base + i + u * stride, v[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t lo = 0, hi = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    lo |= (uint32_t)e4m3_of(v[u][k], s, r) << (8 * k);
+                    hi |= (uint32_t)e4m3_of(v[u][4 + k], s, r) << (8 * k);
+                }
+                *reinterpret_cast<uint2 *>(out + base + i + u * stride) = make_uint2(lo, hi);
+            }
+        }
+        for (; i < len; i += stride) {
             float v[8];
             load8(in + base + i, v);
             uint32_t lo = 0, hi = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                lo |= (uint32_t)e4m3_of(v[k], s) << (8 * k);
-                hi |= (uint32_t)e4m3_of(v[4 + k], s) << (8 * k);
+                lo |= (uint32_t)e4m3_of(v[k], s, r) << (8 * k);
+                hi |= (uint32_t)e4m3_of(v[4 + k], s, r) << (8 * k);
             }
             *reinterpret_cast<uint2 *>(out + base + i) = make_uint2(lo, hi);
         }
     } else {
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < len;
              i += (long long)gridDim.x * blockDim.x)
-            out[base + i] = e4m3_of(to_f(in[base + i]), s);
+            out[base + i] = e4m3_of(to_f(in[base + i]), s, r);
     }
 }
 

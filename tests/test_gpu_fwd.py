@@ -240,6 +240,49 @@ def test_quantize_e4m3_large_tensor_matches_oracle(n, dt):
     assert np.array_equal(got[nz], codes[nz])
 
 
+def _e4m3_midpoints():
+    """Every midpoint between consecutive non-negative E4M3 values up to 448."""
+    vals = np.unique(np.abs(oracle.e4m3_to_f64(np.arange(256, dtype=np.uint8))))
+    vals = vals[np.isfinite(vals) & (vals <= 448)]
+    return (vals[:-1] + vals[1:]) / 2
+
+
+@pytest.mark.parametrize("length", [4096, 4093], ids=["vector", "scalar"])
+def test_quantize_e4m3_near_rounding_midpoints(length):
+    """Quotients v/s at and within three binary32 steps of every E4M3
+    rounding midpoint, both signs, eight rows with their own scales: the
+    GPU's binary32 quotient and E4M3 code equal the oracle's for each (the
+    ties of either rounding are where a wrong quotient would show)."""
+    rng = np.random.default_rng(11)
+    mids = _e4m3_midpoints().astype(np.float32)
+    rows = 8
+    t = np.zeros((rows, length), dtype=np.float32)
+    for r in range(rows):
+        amax = np.float32(rng.uniform(0.5, 4.0) * 10.0 ** rng.integers(-3, 4))
+        s = np.float32(amax / np.float32(448.0))
+        vals = [amax]
+        for m in mids:
+            v = np.float32(m * s)
+            for k in range(-3, 4):
+                w = v
+                for _ in range(abs(k)):
+                    w = np.nextafter(w, np.float32(np.inf if k > 0 else -np.inf), dtype=np.float32)
+                if abs(w) <= amax:
+                    vals += [w, -w]
+        vals = np.array(vals, dtype=np.float32)
+        assert len(vals) <= length
+        t[r, :len(vals)] = vals
+    q, sc = F.quantize_e4m3(torch.from_numpy(t).cuda(), rows=rows)
+    F.device_error()
+    codes, scales = oracle.scale_quant_e4m3(t, rows)
+    assert np.array_equal(sc.cpu().numpy(), scales)
+    got = q.view(torch.uint8).cpu().numpy().reshape(-1)
+    codes = codes.reshape(-1)
+    assert np.array_equal(oracle.e4m3_to_f64(got), oracle.e4m3_to_f64(codes))
+    nz = oracle.e4m3_to_f64(codes) != 0
+    assert np.array_equal(got[nz], codes[nz])
+
+
 @pytest.mark.parametrize("sh", [ConvShape(2, 32, 9, 9, 32, 3, 3, 1, 1, 1),
                                 ConvShape(3, 128, 10, 10, 64, 3, 3, 1, 1, 1),
                                 ConvShape(2, 144, 8, 8, 40, 1, 1, 1, 0, 1),
