@@ -157,8 +157,8 @@ gbconv_status_t gbconv_output_dims(const gbconv_problem_t *prob, int32_t *P, int
 /* Bytes of device workspace `op` needs for `prob` (0 when none). Host only.
  * FWD: 0. DGRAD: the filter rotated by 180 degrees with C and K exchanged
  * (tensor-core path, stride 1), rounded up to 256 bytes; 0 otherwise.
- * WGRAD: (split_k * K*R*S*C/G + 128 * K) fp32 partial sums (weight slices
- * and 128 bias slices), rounded up to 256 bytes. */
+ * WGRAD: (split_k * K*R*S*C/G + 304 * K) fp32 partial sums (weight slices
+ * and 304 bias slices), rounded up to 256 bytes. */
 gbconv_status_t gbconv_workspace_size(int32_t op, const gbconv_problem_t *prob, size_t *bytes);
 
 /* Forward convolution (paper Sec. 5.B, forward pass of a convolutional layer).

@@ -252,7 +252,7 @@ TcConfig config_for(int op, const gbconv_problem_t &p, const Dims &d) {
 
 // Bias-gradient partial sums: a fixed number of row slices, independent of
 // the weight gradient's split.
-constexpr int BIAS_SLICES = 128;
+constexpr int BIAS_SLICES = 304;  // 2 x 152 SMs
 
 size_t wgrad_ws_bytes(const Dims &d, int slices) {
     size_t kcrs = (size_t)d.K * (d.C / d.G) * d.R * d.S;

@@ -154,7 +154,15 @@ __global__ void reduce_slices_warp(const float *__restrict__ ws, int slices, int
     const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (i >= n) return;  // whole warps
     float sum = 0.f, comp = 0.f;
-    for (int s = lane; s < slices; s += 32) neumaier(sum, comp, ws[(long long)s * n + i]);
+    int s = lane;
+    for (; s + 7 * 32 < slices; s += 8 * 32) {  // eight loads in flight, summed in slice order
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = ws[(long long)(s + 32 * j) * n + i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) neumaier(sum, comp, v[j]);
+    }
+    for (; s < slices; s += 32) neumaier(sum, comp, ws[(long long)s * n + i]);
     float t = sum + comp;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
@@ -529,6 +537,7 @@ gbconv_status_t launch_bias_grad(const Dims &d, const void *g, float *db, float 
         return cuda_status(launch_pdl(reduce_slices_warp, dim3((unsigned)((d.K + 7) / 8)), dim3(256), 0,
                                       st, (const float *)ws, slices, d.K, db));
     }
+    slices = std::min(slices, 128);  // the generic kernels: at most 128 row slices
     if (d.layout == GBCONV_NHWC) {
         dim3 grid((unsigned)((d.K + 31) / 32), (unsigned)slices);
         if (d.in_dtype == GBCONV_F32)
