@@ -38,8 +38,9 @@ struct FastArgs {
     int relu;
 };
 
+// 128x64 tiles fit three blocks per SM (85 registers), 128x128 tiles two.
 template <int BN>
-__global__ void __launch_bounds__(FT, 2) simt_fast_fwd(const FastArgs a) {
+__global__ void __launch_bounds__(FT, BN == 64 ? 3 : 2) simt_fast_fwd(const FastArgs a) {
     constexpr int TN = BN / 16;        // columns per thread (8 or 4)
     constexpr int BV = BN * FK / 4 / FT;  // filter vectors per thread per k-tile (2 or 1)
     __shared__ __align__(16) float As[2][FK][FM + FPAD];
@@ -231,8 +232,12 @@ gbconv_status_t launch_simt_fast_fwd(const Dims &d, const void *x, const void *w
     a.relu = (d.flags & GBCONV_FLAG_RELU) ? 1 : 0;
     const long long mt = (d.M() + FM - 1) / FM;
     if (mt > 0x7fffffffll) return GBCONV_ERR_UNSUPPORTED;
-    if (d.K <= 64) {
+    // 64-wide tiles for K <= 64, and where 128-wide tiles would not fill one
+    // wave of two blocks per SM (the narrow tiles run three per SM)
+    const long long wide = mt * ((d.K + 127) / 128);
+    if (d.K <= 64 || wide < 2LL * sm_count()) {
         dim3 grid((unsigned)mt, (unsigned)((d.K + 63) / 64));
+        if (grid.y > 65535) return GBCONV_ERR_UNSUPPORTED;
         return cuda_status(launch_pdl(simt_fast_fwd<64>, grid, dim3(FT), 0, st, a));
     }
     dim3 grid((unsigned)mt, (unsigned)((d.K + 127) / 128));
