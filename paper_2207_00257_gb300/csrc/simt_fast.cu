@@ -232,10 +232,12 @@ gbconv_status_t launch_simt_fast_fwd(const Dims &d, const void *x, const void *w
     a.relu = (d.flags & GBCONV_FLAG_RELU) ? 1 : 0;
     const long long mt = (d.M() + FM - 1) / FM;
     if (mt > 0x7fffffffll) return GBCONV_ERR_UNSUPPORTED;
-    // 64-wide tiles for K <= 64, and where 128-wide tiles would not fill one
-    // wave of two blocks per SM (the narrow tiles run three per SM)
+    // 64-wide tiles for K <= 64, where 128-wide tiles would not fill one wave
+    // of two blocks per SM, and for short reductions (at most 8 k-tiles: each
+    // CTA is mostly prologue and epilogue, so more of them per SM pay); the
+    // narrow tiles run three per SM
     const long long wide = mt * ((d.K + 127) / 128);
-    if (d.K <= 64 || wide < 2LL * sm_count()) {
+    if (d.K <= 64 || wide < 2LL * sm_count() || a.ktiles <= 8) {
         dim3 grid((unsigned)mt, (unsigned)((d.K + 63) / 64));
         if (grid.y > 65535) return GBCONV_ERR_UNSUPPORTED;
         return cuda_status(launch_pdl(simt_fast_fwd<64>, grid, dim3(FT), 0, st, a));
