@@ -24,7 +24,7 @@
 namespace gbc {
 namespace {
 
-constexpr int FM = 128, FK = 16, FT = 256;
+constexpr int FM = 128, FK = 16, FT = 256;  // FT: threads of the 128-wide tile
 constexpr int FPAD = 4;  // row padding of the shared tiles (floats)
 
 struct FastArgs {
@@ -38,11 +38,19 @@ struct FastArgs {
     int relu;
 };
 
-// 128x64 tiles fit three blocks per SM (85 registers), 128x128 tiles two.
-template <int BN>
-__global__ void __launch_bounds__(FT, BN == 64 ? 3 : 2) simt_fast_fwd(const FastArgs a) {
-    constexpr int TN = BN / 16;        // columns per thread (8 or 4)
-    constexpr int BV = BN * FK / 4 / FT;  // filter vectors per thread per k-tile (2 or 1)
+// NT threads: 16 row groups x NT/16 column groups, 8 x TN outputs each
+// (TN = 16*BN/NT). Per k-step a thread reads 2 + TN/4 16-byte fragments for
+// 8*TN FFMAs: the 8 x 8 forms (128 x 128 on 256 threads, 128 x 64 on 128
+// threads) balance shared-memory wavefronts against FFMA issue, the 8 x 4
+// form (128 x 64 on 256 threads) is bound by shared memory. Blocks per SM:
+// 4 for 128 threads, 3 for 128 x 64 on 256, 2 for 128 x 128 (registers).
+template <int BN, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 4 : (BN == 64 ? 3 : 2))
+    simt_fast_fwd(const FastArgs a) {
+    constexpr int TN = 16 * BN / NT;       // columns per thread (8 or 4)
+    constexpr int RP = NT / 4;             // rows loaded per pass
+    constexpr int AP = FM / RP;            // pixel vectors per thread per k-tile
+    constexpr int BV = BN / RP;            // filter vectors per thread per k-tile
     __shared__ __align__(16) float As[2][FK][FM + FPAD];
     __shared__ __align__(16) float Bs[2][FK][BN + FPAD];
     const int t = threadIdx.x;
@@ -51,13 +59,13 @@ __global__ void __launch_bounds__(FT, BN == 64 ? 3 : 2) simt_fast_fwd(const Fast
     const int n0 = blockIdx.y * BN;
     ptx::griddep_wait();
 
-    // this thread's two pixels (A vectors) and BV filter rows (B vectors)
+    // this thread's AP pixels (A vectors) and BV filter rows (B vectors)
     const int cq = (t & 3) * 4;  // channel quad inside the k-tile
-    int xbase[2];
-    int hb[2], wb[2];
+    int xbase[AP];
+    int hb[AP], wb[AP];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int m = m0 + (t >> 2) + 64 * i;
+    for (int i = 0; i < AP; ++i) {
+        const int m = m0 + (t >> 2) + RP * i;
         if (m < a.M) {
             const int q = m % a.Q;
             const int r = m / a.Q;
@@ -74,14 +82,14 @@ __global__ void __launch_bounds__(FT, BN == 64 ? 3 : 2) simt_fast_fwd(const Fast
     }
     int krow[BV];
 #pragma unroll
-    for (int i = 0; i < BV; ++i) krow[i] = n0 + (t >> 2) + 64 * i;
+    for (int i = 0; i < BV; ++i) krow[i] = n0 + (t >> 2) + RP * i;
 
-    float4 ra[2], rb[BV];
+    float4 ra[AP], rb[BV];
     auto load = [&](int kt) {
         const int rs = kt / a.cb, c = (kt - rs * a.cb) * FK + cq;
         const int r = rs / a.S, s = rs - r * a.S;
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < AP; ++i) {
             const int h = hb[i] + r * a.dh, ww = wb[i] + s * a.dw;
             const bool ok = c < a.C && h >= 0 && h < a.H && ww >= 0 && ww < a.W;
             ra[i] = ok ? __ldg(reinterpret_cast<const float4 *>(
@@ -98,18 +106,18 @@ __global__ void __launch_bounds__(FT, BN == 64 ? 3 : 2) simt_fast_fwd(const Fast
     auto store = [&](int buf) {
         const int mr = t >> 2;
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            As[buf][cq + 0][mr + 64 * i] = ra[i].x;
-            As[buf][cq + 1][mr + 64 * i] = ra[i].y;
-            As[buf][cq + 2][mr + 64 * i] = ra[i].z;
-            As[buf][cq + 3][mr + 64 * i] = ra[i].w;
+        for (int i = 0; i < AP; ++i) {
+            As[buf][cq + 0][mr + RP * i] = ra[i].x;
+            As[buf][cq + 1][mr + RP * i] = ra[i].y;
+            As[buf][cq + 2][mr + RP * i] = ra[i].z;
+            As[buf][cq + 3][mr + RP * i] = ra[i].w;
         }
 #pragma unroll
         for (int i = 0; i < BV; ++i) {
-            Bs[buf][cq + 0][mr + 64 * i] = rb[i].x;
-            Bs[buf][cq + 1][mr + 64 * i] = rb[i].y;
-            Bs[buf][cq + 2][mr + 64 * i] = rb[i].z;
-            Bs[buf][cq + 3][mr + 64 * i] = rb[i].w;
+            Bs[buf][cq + 0][mr + RP * i] = rb[i].x;
+            Bs[buf][cq + 1][mr + RP * i] = rb[i].y;
+            Bs[buf][cq + 2][mr + RP * i] = rb[i].z;
+            Bs[buf][cq + 3][mr + RP * i] = rb[i].w;
         }
     };
 
@@ -140,7 +148,7 @@ __global__ void __launch_bounds__(FT, BN == 64 ? 3 : 2) simt_fast_fwd(const Fast
             bv[2] = b0.z;
             bv[3] = b0.w;
             if constexpr (TN == 8) {
-                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][k][64 + tn * 4]);
+                const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][k][BN / 2 + tn * 4]);
                 bv[4] = b1.x;
                 bv[5] = b1.y;
                 bv[6] = b1.z;
@@ -157,14 +165,14 @@ __global__ void __launch_bounds__(FT, BN == 64 ? 3 : 2) simt_fast_fwd(const Fast
     }
     if (t == 0) ptx::griddep_launch();
 
-    // epilogue: rows tm*4 + i (+64), columns tn*4 + j (+64)
+    // epilogue: rows tm*4 + i (+64), columns tn*4 + j (+BN/2)
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int m = m0 + (i < 4 ? tm * 4 + i : 64 + tm * 4 + (i - 4));
         if (m >= a.M) continue;
 #pragma unroll
         for (int h = 0; h < TN / 4; ++h) {
-            const int k = n0 + 64 * h + tn * 4;
+            const int k = n0 + (BN / 2) * h + tn * 4;
             if (k >= a.K) continue;  // K is a multiple of 4: a vector is all in or all out
             float o[4];
 #pragma unroll
@@ -240,11 +248,11 @@ gbconv_status_t launch_simt_fast_fwd(const Dims &d, const void *x, const void *w
     if (d.K <= 64 || wide < 2LL * sm_count() || a.ktiles <= 8) {
         dim3 grid((unsigned)mt, (unsigned)((d.K + 63) / 64));
         if (grid.y > 65535) return GBCONV_ERR_UNSUPPORTED;
-        return cuda_status(launch_pdl(simt_fast_fwd<64>, grid, dim3(FT), 0, st, a));
+        return cuda_status(launch_pdl(simt_fast_fwd<64, 128>, grid, dim3(128), 0, st, a));
     }
     dim3 grid((unsigned)mt, (unsigned)((d.K + 127) / 128));
     if (grid.y > 65535) return GBCONV_ERR_UNSUPPORTED;
-    return cuda_status(launch_pdl(simt_fast_fwd<128>, grid, dim3(FT), 0, st, a));
+    return cuda_status(launch_pdl(simt_fast_fwd<128, FT>, grid, dim3(FT), 0, st, a));
 }
 
 }  // namespace gbc
